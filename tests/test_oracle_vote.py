@@ -1,0 +1,360 @@
+"""Pins of the oracle's vote, peaks, angle vote and refinement (not gpu).
+
+Each test checks the oracle against something other than itself: hand-derived fixtures,
+an independent geometric formulation of the cell test, Algorithm 1's sampled rasteriser,
+closed forms with noise-free inputs, invariances, or library routines."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+from oracle import vote as ov
+from paper_2502_06337_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _single(d):
+    """A one-correspondence problem whose difference p - q is d (q = 0)."""
+    P = np.asarray([d], dtype=np.float32)
+    Q = np.zeros_like(P)
+    return P, Q
+
+
+def test_golden_unit_circle():
+    want = np.loadtxt(os.path.join(GOLDEN, "unit_circle_G8.txt"), dtype=np.int64)
+    av = oracle.axis_vote(*_single([0, 0, 1]), 8)
+    assert np.array_equal(av["grid"], want)
+    assert np.array_equal(av["lo"], want) and np.array_equal(av["hi"], want)
+
+
+def test_golden_line_through_pole():
+    want = np.loadtxt(os.path.join(GOLDEN, "line_u0_G8.txt"), dtype=np.int64)
+    av = oracle.axis_vote(*_single([1, 0, 0]), 8)
+    assert np.array_equal(av["grid"], want)
+    assert av["lo"].sum() == 0 and np.array_equal(av["hi"], want)
+
+
+def _circle_geometry_cells(d, G):
+    """Independent form of the cell test: the plane circle of centre -(d1, d2)/d3 and radius
+    |d|/|d3| meets a closed box iff (nearest distance) <= radius <= (farthest distance)."""
+    e = ov.grid_edges(G)
+    cx, cy = -d[0] / d[2], -d[1] / d[2]
+    rho = np.linalg.norm(d) / abs(d[2])
+    out = np.zeros((G, G), dtype=bool)
+    for i in range(G):
+        for j in range(G):
+            u0, u1, v0, v1 = e[j], e[j + 1], e[i], e[i + 1]
+            nx = min(max(cx, u0), u1)
+            ny = min(max(cy, v0), v1)
+            near = math.hypot(nx - cx, ny - cy)
+            far = max(math.hypot(x - cx, y - cy) for x in (u0, u1) for y in (v0, v1))
+            out[i, j] = near <= rho <= far
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cell_test_matches_circle_geometry(seed):
+    rng = np.random.default_rng(seed)
+    G = 32
+    for _ in range(4):
+        d = rng.standard_normal(3)
+        if abs(d[2]) < 0.05:
+            continue
+        av = oracle.axis_vote(*_single(d), G)
+        geo = _circle_geometry_cells(d, G)
+        certain = av["lo"] == av["hi"]
+        assert np.array_equal(av["grid"].astype(bool)[certain], geo[certain])
+        assert certain.mean() > 0.99
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_algorithm1_sampled_cells_are_voted(seed):
+    """Every cell hit by Algorithm 1's sampled circle is voted, and with dense sampling the
+    two sets coincide up to cells the curve only grazes."""
+    rng = np.random.default_rng(100 + seed)
+    G = 64
+    for _ in range(3):
+        d = rng.standard_normal(3)
+        av = oracle.axis_vote(*_single(d), G)
+        voted = set(zip(*np.nonzero(av["grid"])))
+        hit = ov.sampled_circle_cells(d, G, 400_000)
+        assert hit <= voted
+        missed = voted - hit
+        assert len(missed) <= max(2, 0.01 * len(voted))
+
+
+def test_line_cells_and_symmetry():
+    G = 16
+    av = oracle.axis_vote(*_single([0, 1, 0]), G)  # the line v = 0: rows 7 and 8
+    want = np.zeros((G, G), dtype=np.int64)
+    want[G // 2 - 1 : G // 2 + 1, :] = 1
+    assert np.array_equal(av["grid"], want)
+
+
+def test_cell_count_sum_and_degenerate():
+    prob = synth.make_problem(200, (0.5,), 0.01, seed=3)
+    P, Q = prob.P.copy(), prob.Q.copy()
+    Q[:5] = P[:5]  # five exact degenerate pairs
+    G = 32
+    av = oracle.axis_vote(P, Q, G)
+    assert av["n_degenerate"] == 5
+    total = 0
+    for i in range(5, 200):
+        Fmin, Fmax = ov.circle_cell_extrema(P[i].astype(np.float64) - Q[i], G)
+        total += int(((Fmin <= 0) & (Fmax >= 0)).sum())
+    assert av["grid"].sum() == total
+
+
+def test_noise_free_axis_cell_gets_every_vote():
+    """sigma = 0: every inlier circle passes through the true axis, so the cell holding the
+    projected axis gets one vote per pair and is the peak (Fig. 3a)."""
+    for seed in range(4):
+        prob = synth.make_problem(300, (1.0,), 0.0, seed=seed)
+        R = prob.rotations[0]
+        rv = Rotation.from_matrix(R).as_rotvec()
+        r = rv / np.linalg.norm(rv)
+        if r[2] > 0:
+            r = -r
+        A, B = oracle.stereographic_projection(r)
+        G = 64
+        col, row = int((A + 1) * G / 2), int((B + 1) * G / 2)
+        av = oracle.axis_vote(prob.P, prob.Q, G)
+        nondeg = prob.n - av["n_degenerate"]
+        assert av["grid"][row, col] == nondeg
+        assert av["grid"].max() == nondeg
+
+
+def test_peak_tie_break():
+    g = np.zeros((4, 4), dtype=np.int64)
+    g[2, 1] = 5
+    g[1, 3] = 5
+    assert oracle.peak_cell(g) == (1, 3, 5)
+
+
+def test_top_k_suppression_by_construction():
+    G = 256  # near the centre one cell spans about 0.9 degrees
+    g = np.zeros((G, G), dtype=np.int64)
+    g[128, 128] = 100  # peak 1
+    g[128, 129] = 90   # neighbour of peak 1: within 2 degrees, suppressed
+    g[129, 128] = 80
+    g[40, 200] = 70    # far away: peak 2
+    g[40, 201] = 69    # neighbour of peak 2
+    g[200, 20] = 60    # peak 3
+    peaks = oracle.top_k_cells(g, 3, 2.0)
+    assert peaks == [(128, 128, 100), (40, 200, 70), (200, 20, 60)]
+    assert oracle.top_k_cells(g, 3, 0.0) == [(128, 128, 100), (128, 129, 90), (129, 128, 80)]
+    assert oracle.top_k_cells(np.zeros((8, 8), dtype=np.int64), 2, 2.0) == []
+
+
+def test_top_k_suppresses_antipodal_axis():
+    """Axis lines: a corner cell outside the unit disk and the disk cell of the opposite
+    direction are one axis, so the second is suppressed."""
+    G = 64
+    g = np.zeros((G, G), dtype=np.int64)
+    g[0, 0] = 50  # corner, centre (-63/64, -63/64): northern hemisphere
+    r = oracle.inverse_stereographic_projection(-1 + 1 / G, -1 + 1 / G)
+    A, B = oracle.stereographic_projection(-r)
+    col, row = int((A + 1) * G / 2), int((B + 1) * G / 2)
+    g[row, col] = 40
+    peaks = oracle.top_k_cells(g, 2, 2.0)
+    assert peaks == [(0, 0, 50)]
+
+
+def test_cell_axis_is_south_and_unit():
+    for G in (16, 64):
+        for row in range(0, G, 5):
+            for col in range(0, G, 7):
+                r = oracle.cell_axis(G, row, col)
+                assert abs(np.linalg.norm(r) - 1) < 1e-14 and r[2] <= 0
+
+
+def test_pair_angles_closed_form():
+    """q = R(r, theta) p exactly: the per-pair angle is theta for every p off the axis,
+    with the sign convention of Eq. 2."""
+    rng = np.random.default_rng(9)
+    for _ in range(30):
+        r = rng.standard_normal(3)
+        r /= np.linalg.norm(r)
+        th = rng.uniform(-math.pi + 1e-3, math.pi - 1e-3)
+        P = rng.uniform(-1, 1, (100, 3))
+        Q = P @ oracle.rodrigues(r, th).T
+        ang, nb, ng = ov.pair_angles(r, P, Q)
+        assert np.allclose(ang, th, atol=1e-10)
+        ang2, _, _ = ov.pair_angles(-r, P, Q)
+        assert np.allclose(ang2, -th, atol=1e-10)
+
+
+def test_angle_bins_by_construction():
+    """Pairs built at chosen angles fall in the bins the bin rule gives by hand."""
+    J = 8  # bins of 45 degrees starting at -180
+    r = np.array([0.0, 0.0, -1.0])
+    want_deg = [-170, -100, -1, 1, 44, 46, 170]
+    want_bin = [0, 1, 3, 4, 4, 5, 7]
+    P = np.tile([[1.0, 0.0, 0.3]], (len(want_deg), 1))
+    Q = np.stack([oracle.rodrigues(r, math.radians(a)) @ P[0] for a in want_deg])
+    gate = np.ones(len(P), dtype=bool)
+    av = oracle.angle_vote(P, Q, r, gate, np.zeros_like(gate), J)
+    assert av["bin"].tolist() == want_bin
+    assert av["hist"].tolist() == [1, 1, 0, 1, 2, 1, 0, 1]
+    b, th = oracle.angle_peak(av["hist"])
+    assert b == 4 and math.isclose(th, math.radians(22.5))
+
+
+def test_window_gate_matches_cells():
+    """The gate is the closed-box test on the window, i.e. 'some cell of the window voted'."""
+    prob = synth.make_problem(150, (0.5,), 0.01, seed=11)
+    G = 32
+    for (row, col, w) in [(10, 12, 1), (0, 0, 1), (31, 5, 2), (16, 16, 0)]:
+        gate, flag = oracle.window_gate(prob.P, prob.Q, G, row, col, w)
+        r0, r1 = max(0, row - w), min(G - 1, row + w)
+        c0, c1 = max(0, col - w), min(G - 1, col + w)
+        for i in range(prob.n):
+            d = prob.P[i].astype(np.float64) - prob.Q[i]
+            Fmin, Fmax = ov.circle_cell_extrema(d, G)
+            any_cell = bool(((Fmin <= 0) & (Fmax >= 0))[r0 : r1 + 1, c0 : c1 + 1].any())
+            if not flag[i]:
+                assert gate[i] == any_cell
+
+
+def test_kabsch_is_optimal_and_proper():
+    rng = np.random.default_rng(12)
+    for _ in range(10):
+        P = rng.standard_normal((40, 3))
+        Q = rng.standard_normal((40, 3))
+        R = oracle.kabsch(P, Q)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - 1) < 1e-12
+        M = Q.T @ P
+        best = np.trace(R.T @ M)
+        for S in Rotation.random(2000, random_state=rng).as_matrix():
+            assert np.trace(S.T @ M) <= best + 1e-9
+
+
+def test_kabsch_exact_recovery():
+    rng = np.random.default_rng(13)
+    R = Rotation.random(random_state=rng).as_matrix()
+    P = rng.uniform(-1, 1, (50, 3))
+    assert np.allclose(oracle.kabsch(P, P @ R.T), R, atol=1e-13)
+
+
+def test_noise_free_solve_is_exact():
+    """sigma = 0 with outliers: the refined rotation is R_gt to rounding when no outlier
+    lands within tau of R_gt p (checked; such seeds are skipped)."""
+    done = 0
+    for seed in range(8):
+        prob = synth.make_problem(400, (0.6,), 0.0, seed=seed)
+        R = prob.rotations[0]
+        res = np.linalg.norm(prob.Q.astype(np.float64) - prob.P @ R.T, axis=1)
+        if np.any((prob.truth < 0) & (res <= 0.05)):
+            continue
+        out = oracle.solve(prob.P, prob.Q, G=64, J=180, tau=0.05)
+        rot = out["rotations"][0]
+        # float32 storage of q = R p limits the exactness to ~1e-7
+        assert oracle.rotation_error(R, rot["R"]) < 1e-6
+        assert np.array_equal(out["labels"] >= 0, prob.truth >= 0)
+        done += 1
+    assert done >= 4
+
+
+def test_swap_invariance():
+    """Swapping P and Q keeps every circle (d -> -d), mirrors the angle histogram
+    (theta -> -theta) and transposes the rotation."""
+    prob = synth.make_problem(300, (0.5,), 0.01, seed=21)
+    G, J = 64, 90
+    a = oracle.solve(prob.P, prob.Q, G, J)
+    b = oracle.solve(prob.Q, prob.P, G, J)
+    assert np.array_equal(a["axis"]["grid"], b["axis"]["grid"])
+    ha = a["rotations"][0]["vote"]["hist"]
+    hb = b["rotations"][0]["vote"]["hist"]
+    assert np.array_equal(ha, hb[::-1])
+    assert oracle.rotation_error(a["rotations"][0]["R"].T, b["rotations"][0]["R"]) < 1e-9
+
+
+def test_permutation_invariance():
+    prob = synth.make_problem(300, (0.5,), 0.01, seed=22)
+    perm = np.random.default_rng(0).permutation(300)
+    G = 64
+    a = oracle.axis_vote(prob.P, prob.Q, G)
+    b = oracle.axis_vote(prob.P[perm], prob.Q[perm], G)
+    assert np.array_equal(a["grid"], b["grid"])
+
+
+def test_conjugation_equivariance():
+    """Rotating both point sets by S conjugates the answer: R -> S R S^T (to the noise)."""
+    prob = synth.make_problem(600, (0.5,), 0.005, seed=23)
+    S = Rotation.from_rotvec([0.3, -0.2, 0.5]).as_matrix()
+    a = oracle.solve(prob.P, prob.Q, 64, 180)
+    Ps = (prob.P.astype(np.float64) @ S.T).astype(np.float32)
+    Qs = (prob.Q.astype(np.float64) @ S.T).astype(np.float32)
+    b = oracle.solve(Ps, Qs, 64, 180)
+    Ra = a["rotations"][0]["R"]
+    Rb = b["rotations"][0]["R"]
+    assert oracle.rotation_error(S @ Ra @ S.T, Rb) < 2e-3
+
+
+def test_small_workload_accuracy():
+    """The 1000-pair, 50 % outlier workload: the refined rotation is within noise of R_gt."""
+    cfg = synth.SMALL
+    prob = synth.make_problem(cfg["n"], cfg["inlier_fracs"], cfg["sigma"], seed=0)
+    out = oracle.solve(prob.P, prob.Q, cfg["grid"], cfg["angle_bins"], tau=synth.default_tau(0.01))
+    err = oracle.rotation_error(prob.rotations[0], out["rotations"][0]["R"])
+    assert err < math.radians(0.2)
+    # the vote rotation itself is within a couple of cells / bins
+    assert oracle.rotation_error(prob.rotations[0], out["rotations"][0]["R_vote"]) < math.radians(3)
+
+
+def test_two_rotations_give_two_peaks():
+    """Fig. 3d-f: with two rotations the accumulator has two peaks, one per axis."""
+    prob = synth.make_problem(1200, (0.35, 0.35), 0.005, seed=31)
+    out = oracle.solve(prob.P, prob.Q, G=64, J=180, k=2, nms_deg=4.0, tau=0.05)
+    assert len(out["rotations"]) == 2
+    errs = sorted(
+        min(oracle.rotation_error(Rg, x["R"]) for x in out["rotations"]) for Rg in prob.rotations
+    )
+    assert errs[-1] < math.radians(0.5)
+
+
+def test_golden_small_regression():
+    """Fixture written by tests/golden/make_golden.py (oracle only)."""
+    import json
+
+    with open(os.path.join(GOLDEN, "small_seed0.json")) as f:
+        g = json.load(f)
+    cfg = synth.SMALL
+    prob = synth.make_problem(cfg["n"], cfg["inlier_fracs"], cfg["sigma"], seed=0)
+    out = oracle.solve(prob.P, prob.Q, cfg["grid"], cfg["angle_bins"], tau=g["tau"])
+    rot = out["rotations"][0]
+    assert list(rot["cell"]) == g["cell"]
+    assert rot["axis_votes"] == g["axis_votes"]
+    assert rot["bin"] == g["bin"]
+    assert int(out["labels"].__ge__(0).sum()) == g["n_inliers"]
+    assert np.allclose(rot["R"], np.array(g["R"]), atol=1e-12)
+
+
+@pytest.mark.parametrize("swap", [False, True])
+def test_cap_between_corners_is_voted(swap):
+    """A cell that the circle enters only with its topmost point, between the two corners of
+    its bottom edge: all four corners lie outside the circle, yet the point (0.125, 0.251) of
+    the curve is inside the cell, so the cell is voted. Built by hand for G = 8: centre
+    (0.125, -x) and radius sqrt(0.125^2 + x^2 + 1) with x = (1.015625 - 0.251^2) / 0.502 put
+    the top of the circle at v = 0.251 (row 5 spans [0.25, 0.5], column 4 spans [0, 0.25]).
+    The swapped case is the same with u and v exchanged (the leftmost-point case)."""
+    x = (1.015625 - 0.251 ** 2) / 0.502
+    d = np.array([-0.125, x, 1.0])
+    row, col = 5, 4
+    if swap:
+        d = d[[1, 0, 2]]
+        row, col = col, row
+    assert abs(oracle.great_circle_curve(d, *((0.251, 0.125) if swap else (0.125, 0.251)))) < 1e-12
+    G = 8
+    e = ov.grid_edges(G)
+    corners = [oracle.great_circle_curve(d, e[col + a], e[row + b]) for a in (0, 1) for b in (0, 1)]
+    assert min(corners) > 0  # every corner outside
+    Fmin, Fmax = ov.circle_cell_extrema(d, G)
+    assert Fmin[row, col] < -1e-3 and Fmax[row, col] > 0
+    av = oracle.axis_vote(np.asarray([d], np.float32), np.zeros((1, 3), np.float32), G)
+    assert av["grid"][row, col] == 1 and av["lo"][row, col] == 1
