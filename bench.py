@@ -1,0 +1,457 @@
+"""Benchmark of the stereographic-projection rotation vote on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sprot|reference] [--no-extras]
+
+A step is one whole solve of the headline workload -- n = 10^6 correspondences, 90 %
+outliers, inlier noise 0.01, 512 x 512 axis grid, 720 angle bins -- through the C ABI:
+axis vote, peak, angle vote, Rodrigues, FP64 refinement and labels. The JSON line reports
+Mcorr/s = n / (device time per step) with inputs resident in HBM (``value``), the same
+through host buffers with the copies inside the timed region (``e2e``), the roofline of the
+axis-vote kernel, the FP64 oracle timed on the host cores on a bounded sample
+(``cpu_baseline``), and, unless --no-extras, the batched (4096 instances) and served
+(Poisson 2000 req/s) forms.
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica of the
+workload: the vote does not need any exchange, so there is no collective on the data path.
+``--impl reference`` times the FP64 oracle (the only reference there is) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mcorr/s axis+angle vote (n=1e6, 90% outl.); served solves/s, p50/p99 ms"
+UNIT = "Mcorr/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sprot", choices=["sprot", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1500,
+                    help="correspondences of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Maximum of a per-rank scalar (the slowest replica sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------
+# the headline workload on the GPU
+# ---------------------------------------------------------------------------------------
+
+def headline_problem(seed):
+    from paper_2502_06337_gb300 import synth
+
+    cfg = synth.HEADLINE
+    prob = synth.make_problem(cfg["n"], cfg["inlier_fracs"], cfg["sigma"], seed=seed)
+    return prob, cfg
+
+
+def run_sprot(args):
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+    from paper_2502_06337_gb300 import build as Bd
+    from paper_2502_06337_gb300 import synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    if not os.path.exists(B.LIB_PATH):
+        Bd.build()
+    B.load()
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+    prob, cfg = headline_problem(seed=rank)
+    n = prob.n
+    G, J, tau = cfg["grid"], cfg["angle_bins"], synth.default_tau(cfg["sigma"])
+    prm = B.make_params(grid=G, angle_bins=J, tau=tau)
+    P = torch.from_numpy(prob.P).to(dev)
+    Q = torch.from_numpy(prob.Q).to(dev)
+    mask = torch.zeros(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return B.estimate_rotation(P, Q, prm, mask=mask)
+
+    for _ in range(max(3, args.warmup)):
+        rot = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = B.launch_count()
+    B.kernel_timing(True)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(st)
+            rot = step()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+    vote_ms, vote_launches = B.kernel_timing_read()
+    B.kernel_timing(False)
+    launches = B.launch_count() - launches0
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t_job = max_over_ranks(t_local, world, dev)
+    value = world * n * args.steps / t_job / 1e6
+    clocks = clk.summary()
+
+    # ---- end to end through host buffers (copies inside the timed region) ----
+    Ph = torch.from_numpy(prob.P).pin_memory()
+    Qh = torch.from_numpy(prob.Q).pin_memory()
+    mh = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    prm_h = B.make_params(grid=G, angle_bins=J, tau=tau, flags=B.HOST_PTRS)
+    Pn, Qn, mn = Ph.numpy(), Qh.numpy(), mh.numpy()
+    for _ in range(2):
+        B.estimate_rotation(Pn, Qn, prm_h, mask=mn)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rot_h = B.estimate_rotation(Pn, Qn, prm_h, mask=mn)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    t_e2e = max_over_ranks(sum(e2e_ms) / 1e3, world, dev)
+    e2e = {"value": world * n * args.steps / t_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(prob.P.nbytes + prob.Q.nbytes),
+           "d2h_bytes_per_step": int(n + 280),
+           "api": "sprot_estimate_rotation(SPROT_HOST_PTRS)"}
+    assert rot_h["cell"] == rot["cell"] and np.array_equal(rot_h["R"], rot["R"])
+
+    # ---- roofline of the axis-vote kernel ----
+    grid = torch.zeros(G * G, dtype=torch.int32, device=dev)
+    B.axis_vote(P, Q, G, grid)
+    torch.cuda.synchronize()
+    increments = int(grid.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+    atomic_peak = B.probe_smem_atomic_rate(4096)
+    vote_s = vote_ms / 1e3 / max(1, vote_launches)
+    achieved = increments / vote_s
+    roofline = {
+        "bound": "alu",
+        "resource": "shared-memory atomic unit (red.shared.add.u32 per voted cell)",
+        "kernel": "k_axis_vote",
+        "achieved": achieved / 1e9,
+        "peak": atomic_peak / 1e9,
+        "unit": "Gatom/s",
+        "frac": achieved / atomic_peak,
+        "peak_source": "measured in this run by sprot_probe_smem_atomic_rate (conflict-free shared atomics on every SM)",
+        "algorithmic_per_launch": increments,
+        "kernel_ms": vote_s * 1e3,
+        "kernel_share_of_step": vote_s * 1e3 / (sum(step_ms) / len(step_ms)),
+        "traffic": None,
+    }
+    prof = os.path.join(ROOT, "profiles", "axis_vote_traffic.json")
+    if os.path.exists(prof):
+        try:
+            roofline["traffic"] = json.load(open(prof)).get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry, u32 votes, f64 refinement",
+        "data": "synthetic (seeded; uniform cube points, uniform random rotation)",
+        "config": {"workload": "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins",
+                   "n": n, "grid": G, "angle_bins": J, "tau": tau, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (512 MB write outside the timed events)"},
+        "result": {"cell": rot["cell"], "bin": rot["bin"], "axis_votes": rot["axis_votes"],
+                   "n_inliers": rot["n_inliers"],
+                   "rot_err_deg_vs_truth": math.degrees(_rot_err(prob.rotations[0], rot["R"]))},
+        "e2e": e2e, "roofline": roofline, "clocks": clocks,
+        "gpu_launches": int(launches), "step_ms_min": min(step_ms), "step_ms_median": float(np.median(step_ms)),
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(prob, G, J, tau, args.cpu_sample)
+        if not args.no_extras:
+            try:
+                out["batched"] = run_batched(B, dev)
+            except Exception as e:  # report, never hide
+                out["batched"] = {"error": repr(e)}
+            try:
+                out["served"] = run_served(B)
+            except Exception as e:
+                out["served"] = {"error": repr(e)}
+        print(json.dumps(out), flush=True)
+    barrier(world)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _rot_err(Ra, Rb):
+    c = 0.5 * (np.trace(np.asarray(Ra).T @ np.asarray(Rb)) - 1.0)
+    return float(np.arccos(np.clip(c, -1.0, 1.0)))
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------------------
+
+def time_oracle(prob, G, J, tau, n_s):
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.solve(prob.P[:n_s], prob.Q[:n_s], G, J, tau=tau)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(prob, G, J, tau, n_s):
+    t = time_oracle(prob, G, J, tau, n_s)
+    return {"value": n_s / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_s} correspondences of the n=1e6 workload (same G={G}, J={J}), "
+                      f"{t:.1f} s; numpy float64, single-threaded element-wise",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2502_06337_gb300 import synth
+
+    prob, cfg = headline_problem(seed=0)
+    G, J, tau = cfg["grid"], cfg["angle_bins"], synth.default_tau(cfg["sigma"])
+    n_s = 200
+    for _ in range(max(1, min(args.warmup, 1))):
+        time_oracle(prob, G, J, tau, n_s)
+    times = [time_oracle(prob, G, J, tau, n_s) for _ in range(args.steps)]
+    t = sum(times)
+    value = n_s * args.steps / t / 1e6
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins",
+                                        "n": prob.n, "grid": G, "angle_bins": J},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: FP64 oracle on the first {n_s} correspondences"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# batched and served forms
+# ---------------------------------------------------------------------------------------
+
+def run_batched(B, dev, m=4096, loop_sample=512):
+    """4096 uneven instances in one batched solve vs a per-instance loop of single solves."""
+    import torch
+
+    from paper_2502_06337_gb300 import synth
+
+    specs = synth.batch_specs(m, seed=0)
+    probs, total = [], 0
+    for s in specs:
+        pb = synth.make_problem(s["n"], s["inlier_fracs"], s["sigma"], seed=s["seed"])
+        tau = synth.default_tau(s["sigma"])
+        P = torch.from_numpy(pb.P).to(dev)
+        Q = torch.from_numpy(pb.Q).to(dev)
+        probs.append((P, Q, B.make_params(grid=0, angle_bins=360, tau=tau), pb))
+        total += s["n"]
+    batch = [(P, Q, prm) for P, Q, prm, _ in probs]
+    B.estimate_batch(batch)  # warm-up (allocates the workspace)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        res, grids = B.estimate_batch(batch)
+    t_batch = (time.perf_counter() - t0) / reps
+    # per-instance loop of the plain single solve on the first loop_sample instances (same params)
+    sub = probs[:loop_sample]
+    for P, Q, prm, _ in sub[:8]:
+        B.estimate_rotations(P, Q, B.make_params(grid=grids[0], angle_bins=360, tau=prm.tau), allow_noaxis=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop_res = []
+    for i, (P, Q, prm, _) in enumerate(sub):
+        p1 = B.make_params(grid=grids[i], angle_bins=360, tau=prm.tau)
+        loop_res.append(B.estimate_rotations(P, Q, p1, allow_noaxis=True))
+    t_loop = (time.perf_counter() - t0) * (m / len(sub))
+    same = all(len(a) == len(b) and all(x["cell"] == y["cell"] and x["bin"] == y["bin"] and
+                                         _rot_err(x["R"], y["R"]) < 1e-9 for x, y in zip(a, b))
+               for a, b in zip(res[:len(sub)], loop_res))
+    errs = [math.degrees(_rot_err(pb.rotations[0], r[0]["R"])) for (_, _, _, pb), r in zip(probs, res) if r]
+    return {"instances": m, "correspondences": total, "batch_s": t_batch,
+            "solves_per_s": m / t_batch, "Mcorr_per_s": total / t_batch / 1e6,
+            "loop_solves_per_s": m / t_loop, "speedup_vs_loop": t_loop / t_batch,
+            "loop_extrapolated_from": len(sub), "same_results_as_loop": bool(same),
+            "median_rot_err_deg": float(np.median(errs)) if errs else None,
+            "frac_rot_err_below_1deg": float(np.mean(np.array(errs) < 1.0)) if errs else None}
+
+
+def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40):
+    """Poisson arrivals into the continuous-batching server; latency from submit to done."""
+    from paper_2502_06337_gb300 import synth
+
+    m = int(duration_s * rate_hz)
+    specs = synth.serve_specs(m, seed=1, rate_hz=rate_hz)
+    # a pool of distinct problems drawn from the same distribution, reused by the arrivals
+    pool_specs = synth.serve_specs(pool, seed=2, rate_hz=rate_hz)
+    probs = []
+    for s in pool_specs:
+        pb = synth.make_problem(s["n"], s["inlier_fracs"], s["sigma"], seed=s["seed"])
+        k = len(s["inlier_fracs"])
+        probs.append((pb, B.make_params(grid=0, angle_bins=360, k=k, nms_deg=2.0, tau=synth.default_tau(0.01))))
+    srv = B.Server(budget_gb << 30, max_batch=256)
+    try:
+        # warm-up
+        for pb, prm in probs[:4]:
+            srv.wait(srv.submit(pb.P, pb.Q, prm))
+        tickets = []
+        t0 = time.perf_counter()
+        for i, s in enumerate(specs):
+            dt = s["t_arrive"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            pb, prm = probs[i % pool]
+            tickets.append((srv.submit(pb.P, pb.Q, prm), i % pool))
+        results = [(srv.wait(t), j) for t, j in tickets]
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r, _ in results])
+    first = min(r["t_submit_ms"] for r, _ in results)
+    last = max(r["t_done_ms"] for r, _ in results)
+    ok = sum(1 for r, _ in results if r["status"] == 0)
+    corr = sum(probs[j][0].n for _, j in results)
+    return {"requests": m, "completed_ok": ok, "offered_rate_hz": rate_hz,
+            "solves_per_s": m / ((last - first) / 1e3), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_n": corr / m,
+            "Mcorr_per_s": corr / ((last - first) / 1e3) / 1e6, "wall_s": wall,
+            "budget_gb": budget_gb, "pool_problems": pool}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_sprot(args)
+
+
+if __name__ == "__main__":
+    main()

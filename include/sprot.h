@@ -1,0 +1,254 @@
+/*
+ * sprot.h -- C ABI of the GB300-native stereographic-projection rotation vote.
+ *
+ * Method: "Accelerating Outlier-robust Rotation Estimation by Stereographic Projection"
+ * (arXiv 2502.06337). Given point sets P = {p_i}, Q = {q_i} and n correspondences with
+ * q_i = R p_i + noise for the inliers (Eq. 1), the estimator
+ *   1. maps every correspondence to the great circle of admissible rotation axes
+ *      {r : r . (p_i - q_i) = 0} (Eqs. 5-8), and that circle by stereographic projection
+ *      from the pole (0,0,1) to a plane circle (Eqs. 11-13);
+ *   2. counts, in a G x G accumulator over the square [-1,1]^2 of the plane, the circles that
+ *      pass through every cell (Algorithm 1; Sec. IV-A), and takes the peak cell -- or the k
+ *      best cells with non-maximum suppression for several rotations (Sec. IV-D) -- whose
+ *      centre, back-projected by Eq. 12, is the axis;
+ *   3. votes the per-pair rotation angle about that axis into J bins over [-pi, pi]
+ *      (Algorithm 1; Sec. IV-B, Eq. 15) and takes the peak bin;
+ *   4. builds R_vote by Rodrigues' formula (Eq. 2; Sec. IV-C), then refines it in FP64 by
+ *      least squares on the inliers (two Kabsch/Horn solves; not part of the paper).
+ *
+ * Conventions shared by every entry point
+ *   - P and Q are n x 3 row-major float32 arrays (x, y, z of each point). They are device
+ *     pointers unless the call's flags contain SPROT_HOST_PTRS, in which case they (and the
+ *     per-pair output arrays) are host pointers and the library copies through pinned
+ *     staging. The library reads P and Q only; the caller owns them and every output buffer.
+ *   - Grid cell (row, col) spans u in [-1 + 2 col/G, -1 + 2 (col+1)/G] and v likewise for
+ *     row; cells are closed, so a circle on a shared edge counts in both cells. Grids are
+ *     row-major uint32 [row][col].
+ *   - Every call is ordered on the CUDA stream it is given (a cudaStream_t passed as void*,
+ *     NULL = the legacy default stream). Calls that return results in host structs
+ *     synchronise that stream before returning. Calls on one stream must not be issued
+ *     concurrently from several host threads; calls on different streams may be.
+ *   - Return value: SPROT_OK (0) or a negative status; sprot_status_string() describes it.
+ *     On error nothing is written to the outputs except where stated.
+ *   - The library allocates its own device workspace (cached per device and stream, grown on
+ *     demand); sprot_release_workspaces() frees it.
+ */
+#ifndef SPROT_H
+#define SPROT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define SPROT_OK 0
+#define SPROT_E_INVAL (-1)   /* bad argument (see each entry point) */
+#define SPROT_E_NOMEM (-2)   /* device or host allocation failed, or over a server budget */
+#define SPROT_E_CUDA (-3)    /* a CUDA runtime call failed */
+#define SPROT_E_TIMEOUT (-4) /* a bounded wait expired */
+#define SPROT_E_NOAXIS (-5)  /* every accumulator cell is zero: no axis can be voted */
+#define SPROT_E_UNIMPL (-6)  /* not implemented */
+#define SPROT_E_BUSY (-7)    /* server queue full or shutting down */
+
+/* ---- flags ------------------------------------------------------------------------------ */
+#define SPROT_HOST_PTRS 0x1u /* P, Q and per-pair outputs are host pointers */
+
+/* ---- limits ----------------------------------------------------------------------------- */
+#define SPROT_MAX_K 8          /* rotations per problem */
+#define SPROT_MIN_GRID 16      /* G is a power of two in [16, 2048] */
+#define SPROT_MAX_GRID 2048
+#define SPROT_MAX_ANGLE_BINS 4096
+
+/* Solver parameters. The paper fixes none of them; the defaults are those of
+ * sprot_default_params(). */
+typedef struct sprot_params {
+  int32_t grid;         /* G: accumulator side, a power of two in [16, 2048] (default 256) */
+  int32_t angle_bins;   /* J: bins over [-pi, pi] (Algorithm 1), 2..4096 (default 360) */
+  int32_t k;            /* rotations sought, 1..SPROT_MAX_K (default 1) */
+  float nms_deg;        /* peaks closer than this (degrees, as axis lines) are suppressed */
+  int32_t gate_window;  /* w: a pair votes an angle only if its circle meets the
+                           (2w+1)^2 cells around the peak; -1 = every pair votes
+                           (Algorithm 1 as printed). Default 1. */
+  int32_t angle_window; /* a: the vote set is the voters within a bins of the peak bin
+                           (circularly). Default 1. */
+  double tau;           /* inlier residual threshold ||q - R p|| <= tau: the "noise level"
+                           input of Algorithm 1 (default 0.05) */
+  uint32_t flags;       /* SPROT_HOST_PTRS */
+} sprot_params;
+
+/* One estimated rotation. Axis/angle/R_vote are the paper's estimate (Sec. IV-C); R_init and
+ * R are the FP64 least-squares refinements (first on the angle-vote set, then on the
+ * residual inliers). */
+typedef struct sprot_rotation {
+  double R[9];          /* refined rotation, row-major */
+  double R_init[9];     /* Kabsch over the angle-vote set */
+  double R_vote[9];     /* Rodrigues(axis, theta) */
+  double axis[3];       /* unit axis (cell centre by Eq. 12), sign chosen so theta in [0,pi] */
+  double theta;         /* bin-centre angle, radians, in [0, pi] */
+  int32_t cell_row, cell_col; /* peak cell */
+  int32_t angle_bin;    /* peak bin of the histogram about the canonical (r_z <= 0) axis */
+  uint32_t axis_votes;  /* count of the peak cell */
+  uint32_t angle_votes; /* count of the peak bin */
+  uint32_t n_vote_set;  /* pairs in the angle-vote set used for R_init */
+  uint32_t n_inliers;   /* pairs labelled with this rotation */
+  uint32_t n_degenerate;/* pairs with p_i == q_i exactly (no circle) */
+} sprot_rotation;
+
+/* Fills the defaults listed in sprot_params. */
+void sprot_default_params(sprot_params* p);
+
+/* Text of a status code (static storage). */
+const char* sprot_status_string(int status);
+
+/* ---- whole-problem solves ----------------------------------------------------------------- */
+
+/* Single rotation (Algorithm 1 end to end plus refinement).
+ *   P, Q         n x 3 float32 (device, or host with SPROT_HOST_PTRS)
+ *   n            number of correspondences, >= 1
+ *   params       non-NULL; params->k is ignored (treated as 1)
+ *   out          host struct, written on success
+ *   inlier_mask  n bytes (device, or host with SPROT_HOST_PTRS), 1 = inlier; may be NULL
+ *   stream       cudaStream_t; synchronised before return
+ * Errors: E_INVAL (NULL pointer, n < 1, bad G/J/tau), E_NOAXIS (all pairs degenerate),
+ *         E_NOMEM, E_CUDA. */
+int sprot_estimate_rotation(const float* P, const float* Q, int64_t n, const sprot_params* params,
+                            sprot_rotation* out, uint8_t* inlier_mask, void* stream);
+
+/* Up to params->k rotations from one accumulator (Sec. IV-D).
+ *   out      host array of params->k structs; the first *n_found are written
+ *   n_found  host int; number of peaks found (peaks with zero votes are not reported)
+ *   labels   n int32 (device, or host with SPROT_HOST_PTRS): rotation index of each pair
+ *            (smallest residual among those <= tau), -1 for outliers; may be NULL
+ * Errors as sprot_estimate_rotation; also E_INVAL for k outside 1..SPROT_MAX_K. */
+int sprot_estimate_rotations_k(const float* P, const float* Q, int64_t n,
+                               const sprot_params* params, sprot_rotation* out, int32_t* n_found,
+                               int32_t* labels, void* stream);
+
+/* Optional intermediate outputs of a solve, for inspection and testing. Every pointer is a
+ * DEVICE pointer or NULL (not written). */
+typedef struct sprot_debug {
+  uint32_t* grid;       /* G*G accumulator, row-major [row][col] */
+  uint32_t* hist;       /* k*J angle histograms (rotation-major), about the canonical axis */
+  int16_t* bins;        /* k*n: bin of each pair about each axis, -1 if it did not vote */
+  uint8_t* vote_set;    /* k*n: 1 if the pair is in that rotation's angle-vote set */
+} sprot_debug;
+
+/* sprot_estimate_rotations_k plus intermediate outputs (dbg may be NULL). */
+int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n,
+                                const sprot_params* params, sprot_rotation* out,
+                                int32_t* n_found, int32_t* labels, const sprot_debug* dbg,
+                                void* stream);
+
+/* ---- stage entry points (device pointers only; asynchronous on the stream) -------------- */
+
+/* Step 2, the accumulator only: grid[G*G] (device uint32) = number of circles of the
+ * non-degenerate pairs passing through each closed cell (Algorithm 1; Fig. 3c). The grid is
+ * overwritten, not accumulated. Errors: E_INVAL (NULL, n < 1, bad G), E_NOMEM, E_CUDA. */
+int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size,
+                    uint32_t* grid, void* stream);
+
+/* Greedy top-k of a grid with non-maximum suppression (Sec. IV-D), on the device:
+ * cells[2*i] = row, cells[2*i+1] = col, counts[i] = votes of peak i, for i < *n_found
+ * (n_found a device int32). Ties go to the smallest row-major index. */
+int sprot_select_peaks(const uint32_t* grid, int32_t grid_size, int32_t k, float nms_deg,
+                       int32_t* cells, uint32_t* counts, int32_t* n_found, void* stream);
+
+/* ---- batched solve ------------------------------------------------------------------------ */
+
+/* One independent problem of a batch. P, Q, labels are device pointers. */
+typedef struct sprot_instance {
+  const float* P;
+  const float* Q;
+  int64_t n;
+  sprot_params params;  /* params.grid may be 0: the autotuner picks G from n */
+  sprot_rotation* out;  /* HOST array of params.k entries */
+  int32_t* n_found;     /* HOST int */
+  int32_t* labels;      /* device n int32, or NULL */
+} sprot_instance;
+
+/* Solves m independent problems with one set of launches over a segmented work queue
+ * (persistent axis-vote kernel, per-instance accumulators), replayed from a cached CUDA
+ * graph when the batch shape repeats. Results equal those of solving each instance alone
+ * with the same parameters. The chosen G is written back into inst[i].params.grid when it
+ * was 0 (so callers can replay an instance alone).
+ * Errors: E_INVAL (m < 1 or any instance invalid; nothing is solved), E_NOMEM, E_CUDA. */
+int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream);
+
+/* Accumulator side the autotuner picks for n pairs (used when params.grid == 0). */
+int32_t sprot_autotune_grid(int64_t n);
+
+/* ---- serving ------------------------------------------------------------------------------ */
+
+typedef struct sprot_server sprot_server;
+
+typedef struct sprot_server_cfg {
+  size_t device_budget_bytes; /* admission budget for resident request buffers (e.g. 40 GB) */
+  int32_t max_batch;          /* most requests launched together (default 256) */
+  int32_t max_queue;          /* most requests waiting for admission (default 65536) */
+  int32_t device;             /* CUDA device ordinal */
+} sprot_server_cfg;
+
+typedef struct sprot_request {
+  const float* P;       /* HOST n x 3; must stay valid until the request completes */
+  const float* Q;
+  int64_t n;
+  sprot_params params;  /* params.grid may be 0 (autotuned) */
+} sprot_request;
+
+typedef struct sprot_result {
+  int32_t status;       /* SPROT_OK or the request's error */
+  int32_t n_found;
+  sprot_rotation rot[SPROT_MAX_K];
+  double t_submit_ms, t_admit_ms, t_done_ms; /* server clock, for latency accounting */
+} sprot_result;
+
+/* Starts a server thread that admits requests while their device buffers fit in the
+ * budget, launches every admitted request together (continuous batching: requests that
+ * arrive while a batch runs join the next one, which overlaps it on a second stream), and
+ * completes each request independently. Errors: E_INVAL, E_NOMEM, E_CUDA. */
+int sprot_server_create(const sprot_server_cfg* cfg, sprot_server** out);
+
+/* Queues a request; *ticket identifies it. E_NOMEM if the request alone exceeds the budget;
+ * E_BUSY if the queue is full or the server is stopping; E_INVAL for bad parameters. */
+int sprot_server_submit(sprot_server* s, const sprot_request* req, uint64_t* ticket);
+
+/* Waits up to timeout_ms (-1 = forever) for a request; on completion copies its result and
+ * forgets the ticket. E_TIMEOUT if not done in time (the ticket stays valid); E_INVAL for an
+ * unknown ticket. */
+int sprot_server_wait(sprot_server* s, uint64_t ticket, int32_t timeout_ms, sprot_result* res);
+
+/* Drains the queue (every queued request completes), stops the thread and frees all
+ * resources. */
+int sprot_server_destroy(sprot_server* s);
+
+/* ---- housekeeping and measurement ----------------------------------------------------------- */
+
+/* Frees every cached device workspace of the calling process (device memory returned). */
+void sprot_release_workspaces(void);
+
+/* Number of kernels this library has launched in the process (monotone counter). */
+uint64_t sprot_kernel_launch_count(void);
+
+/* Kernel timing for measurement: while enabled, CUDA events recorded on the launching stream
+ * bracket every axis-vote kernel launch, and their elapsed times are accumulated (the events
+ * are read when the call that launched the kernel synchronises). enable = 1 turns it on and
+ * clears the totals, 0 turns it off. */
+void sprot_kernel_timing(int enable);
+
+/* Accumulated axis-vote kernel time (ms) and launch count since timing was enabled. */
+void sprot_kernel_timing_read(double* vote_ms, uint64_t* vote_launches);
+
+/* Shared-memory atomic throughput probe: every CTA of a full-chip launch performs
+ * iters rounds of conflict-free 32-bit shared atomic adds (one per thread per round).
+ * Writes the measured atomics per second to *rate (host double). Used to state the roofline
+ * of the axis vote. Synchronises the stream. */
+int sprot_probe_smem_atomic_rate(int32_t iters, double* rate, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPROT_H */

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libsprot (C ABI in include/sprot.h).
+
+Only argument marshalling lives here: every step of the estimator runs in the library's CUDA
+kernels. Device arrays are torch CUDA tensors (torch provides device memory and streams);
+host arrays are numpy arrays used with the SPROT_HOST_PTRS flag. ``load()`` raises if the
+library has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsprot.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOAXIS, E_UNIMPL, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
+HOST_PTRS = 0x1
+MAX_K = 8
+
+EXPORTS = [
+    "sprot_default_params", "sprot_status_string", "sprot_estimate_rotation",
+    "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex", "sprot_axis_vote",
+    "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
+    "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
+    "sprot_release_workspaces", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
+    "sprot_kernel_timing", "sprot_kernel_timing_read",
+]
+
+
+class Params(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("angle_bins", C.c_int32), ("k", C.c_int32),
+                ("nms_deg", C.c_float), ("gate_window", C.c_int32), ("angle_window", C.c_int32),
+                ("tau", C.c_double), ("flags", C.c_uint32)]
+
+
+class Rotation(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("R_init", C.c_double * 9), ("R_vote", C.c_double * 9),
+                ("axis", C.c_double * 3), ("theta", C.c_double), ("cell_row", C.c_int32),
+                ("cell_col", C.c_int32), ("angle_bin", C.c_int32), ("axis_votes", C.c_uint32),
+                ("angle_votes", C.c_uint32), ("n_vote_set", C.c_uint32), ("n_inliers", C.c_uint32),
+                ("n_degenerate", C.c_uint32)]
+
+    def to_dict(self) -> dict:
+        return dict(
+            R=np.array(self.R[:]).reshape(3, 3), R_init=np.array(self.R_init[:]).reshape(3, 3),
+            R_vote=np.array(self.R_vote[:]).reshape(3, 3), axis=np.array(self.axis[:]),
+            theta=float(self.theta), cell=(int(self.cell_row), int(self.cell_col)),
+            bin=int(self.angle_bin), axis_votes=int(self.axis_votes),
+            angle_votes=int(self.angle_votes), n_vote_set=int(self.n_vote_set),
+            n_inliers=int(self.n_inliers), n_degenerate=int(self.n_degenerate))
+
+
+class Debug(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("hist", C.c_void_p), ("bins", C.c_void_p),
+                ("vote_set", C.c_void_p)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("P", C.c_void_p), ("Q", C.c_void_p), ("n", C.c_int64), ("params", Params),
+                ("out", C.POINTER(Rotation)), ("n_found", C.POINTER(C.c_int32)),
+                ("labels", C.c_void_p)]
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_size_t), ("max_batch", C.c_int32),
+                ("max_queue", C.c_int32), ("device", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("P", C.c_void_p), ("Q", C.c_void_p), ("n", C.c_int64), ("params", Params)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_found", C.c_int32), ("rot", Rotation * MAX_K),
+                ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
+class SprotError(RuntimeError):
+    def __init__(self, status: int, what: str, text: str):
+        super().__init__(f"{what}: {text} ({status})")
+        self.status = status
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libsprot.so (built by ``paper_2502_06337_gb300.build``) and declares its ABI."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_2502_06337_gb300.build.build() first")
+    lib = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    lib.sprot_default_params.argtypes = [C.POINTER(Params)]
+    lib.sprot_default_params.restype = None
+    lib.sprot_status_string.argtypes = [C.c_int]
+    lib.sprot_status_string.restype = C.c_char_p
+    lib.sprot_estimate_rotation.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(Rotation), vp, vp]
+    lib.sprot_estimate_rotations_k.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(Rotation),
+                                               C.POINTER(i32), vp, vp]
+    lib.sprot_estimate_rotations_ex.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(Rotation),
+                                                C.POINTER(i32), vp, C.POINTER(Debug), vp]
+    lib.sprot_axis_vote.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.sprot_select_peaks.argtypes = [vp, i32, i32, C.c_float, vp, vp, vp, vp]
+    lib.sprot_estimate_batch.argtypes = [C.POINTER(Instance), i64, vp]
+    lib.sprot_autotune_grid.argtypes = [i64]
+    lib.sprot_autotune_grid.restype = i32
+    lib.sprot_server_create.argtypes = [C.POINTER(ServerCfg), C.POINTER(vp)]
+    lib.sprot_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+    lib.sprot_server_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(Result)]
+    lib.sprot_server_destroy.argtypes = [vp]
+    lib.sprot_release_workspaces.argtypes = []
+    lib.sprot_release_workspaces.restype = None
+    lib.sprot_kernel_launch_count.argtypes = []
+    lib.sprot_kernel_launch_count.restype = C.c_uint64
+    lib.sprot_probe_smem_atomic_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
+    lib.sprot_kernel_timing.argtypes = [C.c_int]
+    lib.sprot_kernel_timing.restype = None
+    lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
+    lib.sprot_kernel_timing_read.restype = None
+    for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
+                 "sprot_axis_vote", "sprot_select_peaks", "sprot_estimate_batch",
+                 "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
+                 "sprot_server_destroy", "sprot_probe_smem_atomic_rate"]:
+        getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def status_text(status: int) -> str:
+    return load().sprot_status_string(status).decode()
+
+
+def check(status: int, what: str, allowed=()):
+    if status != OK and status not in allowed:
+        raise SprotError(status, what, status_text(status))
+    return status
+
+
+def make_params(grid=256, angle_bins=360, k=1, nms_deg=2.0, gate_window=1, angle_window=1,
+                tau=0.05, flags=0) -> Params:
+    return Params(int(grid), int(angle_bins), int(k), float(nms_deg), int(gate_window),
+                  int(angle_window), float(tau), int(flags))
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _check_points(P, Q):
+    import torch
+
+    for X in (P, Q):
+        if isinstance(X, np.ndarray):
+            assert X.dtype == np.float32 and X.ndim == 2 and X.shape[1] == 3 and X.flags.c_contiguous
+        else:
+            assert isinstance(X, torch.Tensor) and X.dtype == torch.float32 and X.is_contiguous()
+            assert X.dim() == 2 and X.shape[1] == 3
+    assert P.shape == Q.shape
+
+
+def estimate_rotation(P, Q, params: Params, mask=None, stream=None):
+    """One rotation (k = 1). P, Q: device tensors, or numpy arrays with HOST_PTRS set in
+    params.flags. ``mask``: optional n-byte output (uint8 tensor / array)."""
+    _check_points(P, Q)
+    lib = load()
+    out = Rotation()
+    st = lib.sprot_estimate_rotation(_ptr(P), _ptr(Q), P.shape[0], C.byref(params), C.byref(out),
+                                     _ptr(mask), _stream(stream))
+    check(st, "sprot_estimate_rotation")
+    return out.to_dict()
+
+
+def estimate_rotations(P, Q, params: Params, labels=None, debug: dict | None = None, stream=None,
+                       allow_noaxis=False):
+    """Up to params.k rotations. ``labels``: optional n int32 output. ``debug``: optional dict
+    of device tensors {'grid': G*G u32 (int32 view), 'hist': k*J, 'bins': k*n int16,
+    'vote_set': k*n uint8} filled with the intermediates. Returns a list of dicts."""
+    _check_points(P, Q)
+    lib = load()
+    outs = (Rotation * max(1, params.k))()
+    nf = C.c_int32(0)
+    dbg = None
+    if debug is not None:
+        dbg = Debug(_ptr(debug.get("grid")), _ptr(debug.get("hist")), _ptr(debug.get("bins")),
+                    _ptr(debug.get("vote_set")))
+    st = lib.sprot_estimate_rotations_ex(_ptr(P), _ptr(Q), P.shape[0], C.byref(params), outs,
+                                         C.byref(nf), _ptr(labels),
+                                         C.byref(dbg) if dbg is not None else None, _stream(stream))
+    check(st, "sprot_estimate_rotations_ex", allowed=(E_NOAXIS,) if allow_noaxis else ())
+    return [outs[a].to_dict() for a in range(nf.value)]
+
+
+def axis_vote(P, Q, G: int, grid, stream=None):
+    """Fills the device tensor ``grid`` (G*G 32-bit) with the accumulator."""
+    _check_points(P, Q)
+    st = load().sprot_axis_vote(_ptr(P), _ptr(Q), P.shape[0], int(G), _ptr(grid), _stream(stream))
+    check(st, "sprot_axis_vote")
+
+
+def select_peaks(grid, G: int, k: int, nms_deg: float, cells, counts, n_found, stream=None):
+    st = load().sprot_select_peaks(_ptr(grid), int(G), int(k), float(nms_deg), _ptr(cells),
+                                   _ptr(counts), _ptr(n_found), _stream(stream))
+    check(st, "sprot_select_peaks")
+
+
+def estimate_batch(problems, stream=None):
+    """problems: list of (P, Q, Params[, labels]) with device tensors. Returns (list of
+    rotation lists, list of the grid sides used)."""
+    lib = load()
+    m = len(problems)
+    insts = (Instance * m)()
+    keep = []
+    for i, pb in enumerate(problems):
+        P, Q, prm = pb[0], pb[1], pb[2]
+        labels = pb[3] if len(pb) > 3 else None
+        _check_points(P, Q)
+        outs = (Rotation * max(1, prm.k))()
+        nf = C.c_int32(0)
+        keep.append((outs, nf))
+        insts[i] = Instance(_ptr(P), _ptr(Q), P.shape[0], prm, outs, C.pointer(nf), _ptr(labels))
+    st = lib.sprot_estimate_batch(insts, m, _stream(stream))
+    check(st, "sprot_estimate_batch")
+    res = [[outs[a].to_dict() for a in range(nf.value)] for outs, nf in keep]
+    return res, [insts[i].params.grid for i in range(m)]
+
+
+class Server:
+    """Continuous-batching server over host requests (sprot_server_*)."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 256, max_queue: int = 65536, device: int = 0):
+        self.lib = load()
+        cfg = ServerCfg(int(budget_bytes), int(max_batch), int(max_queue), int(device))
+        h = C.c_void_p()
+        check(self.lib.sprot_server_create(C.byref(cfg), C.byref(h)), "sprot_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, P: np.ndarray, Q: np.ndarray, params: Params) -> int:
+        _check_points(P, Q)
+        req = Request(_ptr(P), _ptr(Q), P.shape[0], params)
+        t = C.c_uint64(0)
+        check(self.lib.sprot_server_submit(self.h, C.byref(req), C.byref(t)), "sprot_server_submit")
+        self._keep[t.value] = (P, Q)
+        return t.value
+
+    def try_submit(self, P, Q, params: Params):
+        """Like submit, but returns the status instead of raising on NOMEM/BUSY."""
+        req = Request(_ptr(P), _ptr(Q), P.shape[0], params)
+        t = C.c_uint64(0)
+        st = self.lib.sprot_server_submit(self.h, C.byref(req), C.byref(t))
+        if st == OK:
+            self._keep[t.value] = (P, Q)
+        return st, t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        res = Result()
+        st = self.lib.sprot_server_wait(self.h, C.c_uint64(ticket), int(timeout_ms), C.byref(res))
+        if st == E_TIMEOUT:
+            return None
+        check(st, "sprot_server_wait")
+        self._keep.pop(ticket, None)
+        return dict(status=int(res.status), rotations=[res.rot[a].to_dict() for a in range(res.n_found)],
+                    t_submit_ms=res.t_submit_ms, t_admit_ms=res.t_admit_ms, t_done_ms=res.t_done_ms)
+
+    def close(self):
+        if self.h:
+            check(self.lib.sprot_server_destroy(self.h), "sprot_server_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def launch_count() -> int:
+    return int(load().sprot_kernel_launch_count())
+
+
+def probe_smem_atomic_rate(iters: int = 4096, stream=None) -> float:
+    r = C.c_double(0.0)
+    check(load().sprot_probe_smem_atomic_rate(int(iters), C.byref(r), _stream(stream)),
+          "sprot_probe_smem_atomic_rate")
+    return r.value
+
+
+def kernel_timing(enable: bool):
+    load().sprot_kernel_timing(1 if enable else 0)
+
+
+def kernel_timing_read():
+    """(total axis-vote kernel milliseconds, launches) since timing was enabled."""
+    ms, n = C.c_double(0.0), C.c_uint64(0)
+    load().sprot_kernel_timing_read(C.byref(ms), C.byref(n))
+    return ms.value, int(n.value)
+
+
+def release_workspaces():
+    load().sprot_release_workspaces()

@@ -1,0 +1,656 @@
+// Kernels after the axis vote: slice reduction and peak search (Sec. IV-A, IV-D), the angle
+// vote (Algorithm 1 second loop; Sec. IV-B), Rodrigues (Eq. 2) and the FP64 least-squares
+// refinement with labels.
+#include <math_constants.h>
+
+#include "sprot_internal.h"
+
+namespace sprot {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// (count, index) packed so that the maximum key is the largest count, then smallest index.
+__device__ __forceinline__ unsigned long long peak_key(uint32_t count, uint32_t index) {
+  return count ? ((unsigned long long)count << 32) | (0xffffffffu - index) : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__device__ unsigned long long block_max_u64(unsigned long long v) {
+  __shared__ unsigned long long s[32];
+  v = warp_max_u64(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) s[w] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (w == 0) {
+    r = l < (int)(blockDim.x >> 5) ? s[l] : 0ull;
+    r = warp_max_u64(r);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+// Exact axis-line geometry of a cell centre: with a = 2 col + 1 - G and b = 2 row + 1 - G the
+// centre is (a, b)/G, and Eq. 12 gives r = w / N with w = (2aG, 2bG, a^2 + b^2 - G^2) and
+// N = |w| = G^2 + a^2 + b^2 (all integers, exact in double for G <= 2048).
+struct CellAxis {
+  double w0, w1, w2, N;
+};
+__device__ __forceinline__ CellAxis cell_axis(int G, int row, int col) {
+  double a = 2.0 * col + 1.0 - G, b = 2.0 * row + 1.0 - G, g = (double)G;
+  CellAxis c;
+  c.w0 = 2.0 * a * g;
+  c.w1 = 2.0 * b * g;
+  c.w2 = a * a + b * b - g * g;
+  c.N = g * g + a * a + b * b;
+  return c;
+}
+
+// Axis lines of two cells within the suppression radius: |r1 . r2| >= cos(radius).
+__device__ __forceinline__ bool suppressed(const CellAxis& c, const CellAxis& p, double cosr) {
+  double dot = fabs(c.w0 * p.w0 + c.w1 * p.w1 + c.w2 * p.w2);
+  return dot >= cosr * (c.N * p.N);
+}
+
+__global__ void __launch_bounds__(256)
+    k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  const ReduceItem I = items[blockIdx.x];
+  const InstDev& D = insts[I.inst];
+  const int G = D.G, W = G >> 1;
+  const int64_t plane = (int64_t)G * W;
+  unsigned long long best = 0;
+  for (int64_t w = I.w0 + threadIdx.x; w < I.w1; w += blockDim.x) {
+    uint32_t lo = 0, hi = 0;
+    const uint32_t* p = D.partial + w;
+    for (int s = 0; s < D.S; ++s) {
+      uint32_t v = __ldg(p + (int64_t)s * plane);
+      lo += v & 0xffffu;
+      hi += v >> 16;
+    }
+    int row = (int)(w / W), c = (int)(w - (int64_t)row * W);
+    D.grid[(int64_t)row * G + c] = lo;
+    D.grid[(int64_t)row * G + c + W] = hi;
+    unsigned long long k1 = peak_key(lo, (uint32_t)(row * G + c));
+    unsigned long long k2 = peak_key(hi, (uint32_t)(row * G + c + W));
+    best = k1 > best ? k1 : best;
+    best = k2 > best ? k2 : best;
+  }
+  best = block_max_u64(best);
+  if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[0], best);
+}
+
+__global__ void __launch_bounds__(256)
+    k_nms_round(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts, int round) {
+  const ReduceItem I = items[blockIdx.x];
+  const InstDev& D = insts[I.inst];
+  if (round >= D.k) return;
+  __shared__ CellAxis taken[kMaxK];
+  const int G = D.G, W = G >> 1;
+  if (round > 0 && D.peak_key[round - 1] == 0) return;  // fewer peaks than asked for
+  if (threadIdx.x < round) {
+    unsigned long long key = D.peak_key[threadIdx.x];
+    uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+    taken[threadIdx.x] = cell_axis(G, idx / G, idx % G);
+  }
+  __syncthreads();
+  unsigned long long best = 0;
+  // w indexes packed words; each covers cells (row, c) and (row, c + W).
+  for (int64_t w = I.w0 + threadIdx.x; w < I.w1; w += blockDim.x) {
+    int row = (int)(w / W), c0 = (int)(w - (int64_t)row * W);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int col = c0 + h * W;
+      uint32_t cnt = D.grid[(int64_t)row * G + col];
+      if (!cnt) continue;
+      unsigned long long key = peak_key(cnt, (uint32_t)(row * G + col));
+      if (key <= best) continue;
+      CellAxis ca = cell_axis(G, row, col);
+      bool sup = false;
+      for (int t = 0; t < round; ++t) sup |= suppressed(ca, taken[t], D.cos_nms);
+      if (!sup) best = key;
+    }
+  }
+  best = block_max_u64(best);
+  if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[round], best);
+}
+
+__global__ void k_finalize_peaks(const InstDev* __restrict__ insts, int m) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const InstDev& D = insts[i];
+  int found = 0;
+  for (int a = 0; a < D.k; ++a) {
+    unsigned long long key = D.peak_key[a];
+    if (!key) break;
+    uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+    int row = idx / D.G, col = idx % D.G;
+    DevRot& R = D.rot[a];
+    CellAxis c = cell_axis(D.G, row, col);
+    double sgn = c.w2 > 0 ? -1.0 : 1.0;  // canonical: southern hemisphere, r_z <= 0
+    double r0 = sgn * c.w0 / c.N, r1 = sgn * c.w1 / c.N, r2 = sgn * c.w2 / c.N;
+    R.axis[0] = r0;
+    R.axis[1] = r1;
+    R.axis[2] = r2;
+    R.r_cell[0] = (float)r0;
+    R.r_cell[1] = (float)r1;
+    R.r_cell[2] = (float)r2;
+    R.cell_row = row;
+    R.cell_col = col;
+    R.axis_votes = (uint32_t)(key >> 32);
+    ++found;
+  }
+  *D.n_found = found;
+}
+
+// ---- angle vote ------------------------------------------------------------------------
+
+struct PairGeom {
+  float p0, p1, p2, q0, q1, q2;
+  float d1, d2, d3;  // scaled p - q
+  bool deg;
+};
+
+__device__ __forceinline__ void load_pair(const InstDev& D, int64_t i, PairGeom& g) {
+  const float* p = D.P + 3 * i;
+  const float* q = D.Q + 3 * i;
+  g.p0 = __ldg(p);
+  g.p1 = __ldg(p + 1);
+  g.p2 = __ldg(p + 2);
+  g.q0 = __ldg(q);
+  g.q1 = __ldg(q + 1);
+  g.q2 = __ldg(q + 2);
+  float d1 = g.p0 - g.q0, d2 = g.p1 - g.q1, d3 = g.p2 - g.q2;
+  float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
+  g.deg = (m == 0.f);
+  int e = g.deg ? 0 : ilogbf(m);
+  g.d1 = scalbnf(d1, -e);
+  g.d2 = scalbnf(d2, -e);
+  g.d3 = scalbnf(d3, -e);
+}
+
+// min / max of c2 x^2 + c1 x over [lo, hi].
+__device__ __forceinline__ void quad_range(float c2, float c1, float lo, float hi, float& mn,
+                                           float& mx) {
+  float flo = fmaf(c2, lo * lo, c1 * lo);
+  float fhi = fmaf(c2, hi * hi, c1 * hi);
+  mn = fminf(flo, fhi);
+  mx = fmaxf(flo, fhi);
+  // vertex -c1 / (2 c2) inside [lo, hi]: sign tests on 2 c2 x + c1 at the ends
+  float sl = fmaf(2.f * c2, lo, c1), sh = fmaf(2.f * c2, hi, c1);
+  if (c2 != 0.f && ((sl <= 0.f && sh >= 0.f) || (sl >= 0.f && sh <= 0.f))) {
+    float fv = -0.25f * c1 * c1 / c2;
+    mn = fminf(mn, fv);
+    mx = fmaxf(mx, fv);
+  }
+}
+
+struct Window {
+  float u0, u1, v0, v1;
+  float r0, r1, r2;
+};
+
+__global__ void __launch_bounds__(kStreamThreads)
+    k_angle_vote(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts, int J_max) {
+  extern __shared__ uint32_t shist[];  // [k_found][J]
+  __shared__ Window win[kMaxK];
+  __shared__ int s_found;
+  __shared__ unsigned s_deg;
+  const StreamItem I = items[blockIdx.x];
+  const InstDev& D = insts[I.inst];
+  const int J = D.J;
+  if (threadIdx.x == 0) {
+    s_found = *D.n_found;
+    s_deg = 0;
+  }
+  __syncthreads();
+  const int kf = s_found;
+  if (threadIdx.x < kf) {
+    const DevRot& R = D.rot[threadIdx.x];
+    float step = 2.0f / (float)D.G;
+    int w = D.w < 0 ? 0 : D.w;
+    int r0 = max(R.cell_row - w, 0), r1 = min(R.cell_row + w, D.G - 1);
+    int c0 = max(R.cell_col - w, 0), c1 = min(R.cell_col + w, D.G - 1);
+    Window& W = win[threadIdx.x];
+    W.u0 = fmaf((float)c0, step, -1.f);
+    W.u1 = fmaf((float)(c1 + 1), step, -1.f);
+    W.v0 = fmaf((float)r0, step, -1.f);
+    W.v1 = fmaf((float)(r1 + 1), step, -1.f);
+    W.r0 = R.r_cell[0];
+    W.r1 = R.r_cell[1];
+    W.r2 = R.r_cell[2];
+  }
+  for (int t = threadIdx.x; t < kf * J; t += blockDim.x) shist[t] = 0;
+  __syncthreads();
+  const float two_pi = 6.283185307179586f;
+  const float scale = (float)J / two_pi;
+  const float pi_f = 3.14159265358979f;
+  unsigned ndeg = 0;
+  for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
+    PairGeom g;
+    load_pair(D, i, g);
+    ndeg += g.deg;
+    float pp = fmaf(g.p0, g.p0, fmaf(g.p1, g.p1, g.p2 * g.p2));
+    float qq = fmaf(g.q0, g.q0, fmaf(g.q1, g.q1, g.q2 * g.q2));
+    for (int a = 0; a < kf; ++a) {
+      const Window& W = win[a];
+      int bin = -1;
+      if (!g.deg) {
+        bool gate = true;
+        if (D.w >= 0) {
+          float gmin, gmax, hmin, hmax;
+          quad_range(g.d3, 2.f * g.d1, W.u0, W.u1, gmin, gmax);
+          quad_range(g.d3, 2.f * g.d2, W.v0, W.v1, hmin, hmax);
+          gate = (gmin + hmin - g.d3 <= 0.f) && (gmax + hmax - g.d3 >= 0.f);
+        }
+        if (gate) {
+          // beta = r x p, gamma = r x q (Algorithm 1)
+          float b0 = W.r1 * g.p2 - W.r2 * g.p1, b1 = W.r2 * g.p0 - W.r0 * g.p2,
+                b2 = W.r0 * g.p1 - W.r1 * g.p0;
+          float c0 = W.r1 * g.q2 - W.r2 * g.q1, c1 = W.r2 * g.q0 - W.r0 * g.q2,
+                c2 = W.r0 * g.q1 - W.r1 * g.q0;
+          float bb = fmaf(b0, b0, fmaf(b1, b1, b2 * b2));
+          float cc = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+          if (bb > 1e-6f * pp && cc > 1e-6f * qq) {
+            // signed angle: atan2(r . (beta x gamma), beta . gamma)
+            float x0 = b1 * c2 - b2 * c1, x1 = b2 * c0 - b0 * c2, x2 = b0 * c1 - b1 * c0;
+            float sn = fmaf(W.r0, x0, fmaf(W.r1, x1, W.r2 * x2));
+            float cs = fmaf(b0, c0, fmaf(b1, c1, b2 * c2));
+            float th = atan2f(sn, cs);
+            int b = (int)floorf((th + pi_f) * scale);
+            if (b >= J) b -= J;
+            if (b < 0) b += J;
+            bin = b;
+            atomicAdd(&shist[a * J + b], 1u);
+          }
+        }
+      }
+      D.bins[(int64_t)a * D.n + i] = (int16_t)bin;
+    }
+  }
+  atomicAdd(&s_deg, ndeg);
+  __syncthreads();
+  for (int t = threadIdx.x; t < kf * J; t += blockDim.x) {
+    uint32_t v = shist[t];
+    if (v) atomicAdd(&D.hist[t], v);
+  }
+  if (threadIdx.x == 0 && s_deg) atomicAdd(D.n_deg, s_deg);
+}
+
+// Peak bin of each histogram, the bin-centre angle and R_vote by Rodrigues (Eq. 2).
+__global__ void __launch_bounds__(256) k_angle_peak(const InstDev* __restrict__ insts, int max_k) {
+  const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
+  const InstDev& D = insts[inst];
+  if (a >= *D.n_found) return;
+  const int J = D.J;
+  const uint32_t* h = D.hist + (int64_t)a * J;
+  unsigned long long best = 0;
+  for (int b = threadIdx.x; b < J; b += blockDim.x) {
+    unsigned long long key = ((unsigned long long)h[b] << 32) | (0xffffffffu - (uint32_t)b);
+    best = key > best ? key : best;
+  }
+  best = block_max_u64(best);
+  if (threadIdx.x != 0) return;
+  DevRot& R = D.rot[a];
+  int b = (int)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
+  R.angle_bin = b;
+  R.angle_votes = (uint32_t)(best >> 32);
+  double th = -CUDART_PI + (b + 0.5) * (2.0 * CUDART_PI / J);
+  double r0 = R.axis[0], r1 = R.axis[1], r2 = R.axis[2];
+  if (th < 0) {
+    th = -th;
+    r0 = -r0;
+    r1 = -r1;
+    r2 = -r2;
+  }
+  R.axis[0] = r0;
+  R.axis[1] = r1;
+  R.axis[2] = r2;
+  R.theta = th;
+  double s = sin(th), c1 = 1.0 - cos(th);
+  // K = [r]_x ; R = I + s K + (1 - cos) K^2, K^2 = r r^T - I
+  double K[9] = {0, -r2, r1, r2, 0, -r0, -r1, r0, 0};
+  double rr[3] = {r0, r1, r2};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      R.R_vote[3 * i + j] = (i == j ? 1.0 : 0.0) + s * K[3 * i + j] +
+                            c1 * (rr[i] * rr[j] - (i == j ? 1.0 : 0.0));
+}
+
+// ---- FP64 sums of q p^T ----------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Block sum of acc[kMaxK][10] into out (fixed order: warps in index order). All threads call.
+__device__ void block_sums(double (*acc)[10], int kf, double* out) {
+  __shared__ double s[kStreamThreads / 32][10];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int a = 0; a < kf; ++a) {
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+      double v = warp_sum_d(acc[a][t]);
+      if (l == 0) s[w][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+      double v = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += s[i][threadIdx.x];
+      out[a * 10 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void add_qpT(double* acc, const float* p, const float* q) {
+  double p0 = p[0], p1 = p[1], p2 = p[2], q0 = q[0], q1 = q[1], q2 = q[2];
+  acc[0] = fma(q0, p0, acc[0]);
+  acc[1] = fma(q0, p1, acc[1]);
+  acc[2] = fma(q0, p2, acc[2]);
+  acc[3] = fma(q1, p0, acc[3]);
+  acc[4] = fma(q1, p1, acc[4]);
+  acc[5] = fma(q1, p2, acc[5]);
+  acc[6] = fma(q2, p0, acc[6]);
+  acc[7] = fma(q2, p1, acc[7]);
+  acc[8] = fma(q2, p2, acc[8]);
+  acc[9] += 1.0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kStreamThreads)
+    k_vote_set_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  const StreamItem I = items[blockIdx.x];
+  const InstDev& D = insts[I.inst];
+  __shared__ int bhat[kMaxK];
+  __shared__ int s_found;
+  if (threadIdx.x == 0) s_found = *D.n_found;
+  __syncthreads();
+  const int kf = s_found;
+  if (threadIdx.x < kf) bhat[threadIdx.x] = D.rot[threadIdx.x].angle_bin;
+  __syncthreads();
+  double acc[K][10];
+  for (int a = 0; a < K; ++a)
+    for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+  const int J = D.J;
+  for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
+    for (int a = 0; a < kf; ++a) {
+      int b = D.bins[(int64_t)a * D.n + i];
+      bool in = false;
+      if (b >= 0) {
+        int dd = b - bhat[a];
+        if (dd < 0) dd = -dd;
+        dd = min(dd, J - dd);
+        in = dd <= D.window;
+      }
+      if (D.vote_set) D.vote_set[(int64_t)a * D.n + i] = in;
+      if (in) {
+        float p[3] = {D.P[3 * i], D.P[3 * i + 1], D.P[3 * i + 2]};
+        float q[3] = {D.Q[3 * i], D.Q[3 * i + 1], D.Q[3 * i + 2]};
+        // the rotation index is runtime; keep acc in registers by unrolled selection
+#pragma unroll
+        for (int t = 0; t < K; ++t)
+          if (t == a) add_qpT(acc[t], p, q);
+      }
+    }
+  }
+  block_sums(acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
+}
+
+// Residual labels against every R_init (float32 test of ||q - R p||^2 <= tau^2) and the
+// FP64 sums of each label class.
+template <int K>
+__global__ void __launch_bounds__(kStreamThreads)
+    k_label_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  const StreamItem I = items[blockIdx.x];
+  const InstDev& D = insts[I.inst];
+  __shared__ float Rf[kMaxK][9];
+  __shared__ int s_found;
+  if (threadIdx.x == 0) s_found = *D.n_found;
+  __syncthreads();
+  const int kf = s_found;
+  if (threadIdx.x < kf * 9) Rf[threadIdx.x / 9][threadIdx.x % 9] = D.rot[threadIdx.x / 9].R_init_f[threadIdx.x % 9];
+  __syncthreads();
+  double acc[K][10];
+  for (int a = 0; a < K; ++a)
+    for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+  const float tau2 = D.tau * D.tau;
+  for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
+    float p[3] = {D.P[3 * i], D.P[3 * i + 1], D.P[3 * i + 2]};
+    float q[3] = {D.Q[3 * i], D.Q[3 * i + 1], D.Q[3 * i + 2]};
+    int lab = -1;
+    float best = CUDART_INF_F;
+    for (int a = 0; a < kf; ++a) {
+      const float* R = Rf[a];
+      float e0 = q[0] - fmaf(R[0], p[0], fmaf(R[1], p[1], R[2] * p[2]));
+      float e1 = q[1] - fmaf(R[3], p[0], fmaf(R[4], p[1], R[5] * p[2]));
+      float e2 = q[2] - fmaf(R[6], p[0], fmaf(R[7], p[1], R[8] * p[2]));
+      float r2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+      if (r2 <= tau2 && r2 < best) {
+        best = r2;
+        lab = a;
+      }
+    }
+    if (D.labels) D.labels[i] = lab;
+    if (D.mask) D.mask[i] = lab >= 0;
+    if (lab >= 0) {
+#pragma unroll
+      for (int t = 0; t < K; ++t)
+        if (t == lab) add_qpT(acc[t], p, q);
+    }
+  }
+  block_sums(acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
+}
+
+// ---- FP64 rotation from the sums (Horn's unit-quaternion method) --------------------------
+
+// Eigen-decomposition of a symmetric 4x4 matrix by cyclic Jacobi rotations; returns the unit
+// eigenvector of the largest eigenvalue in v.
+__device__ void jacobi4_top(double A[4][4], double v[4]) {
+  double V[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        tot += A[i][j] * A[i][j];
+        if (i != j) off += A[i][j] * A[i][j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        double apq = A[p][q];
+        if (apq == 0.0) continue;
+        double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 4; ++k) {  // A <- A J
+          double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 4; ++k) {  // A <- J^T A
+          double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 4; ++k) {
+          double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  int best = 0;
+  for (int i = 1; i < 4; ++i)
+    if (A[i][i] > A[best][best]) best = i;
+  double n = 0.0;
+  for (int i = 0; i < 4; ++i) n += V[i][best] * V[i][best];
+  n = sqrt(n);
+  for (int i = 0; i < 4; ++i) v[i] = V[i][best] / n;
+}
+
+// Rotation maximising tr(R^T M) for M = sum q p^T: Horn's 4x4 matrix of S = M^T (S_ab =
+// sum p_a q_b), whose top eigenvector is the unit quaternion of the rotation p -> q.
+__device__ void horn_rotation(const double* M, double* R) {
+  double Sxx = M[0], Sxy = M[3], Sxz = M[6];
+  double Syx = M[1], Syy = M[4], Syz = M[7];
+  double Szx = M[2], Szy = M[5], Szz = M[8];
+  double N[4][4] = {
+      {Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx},
+      {Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz},
+      {Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy},
+      {Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz}};
+  double q[4];
+  jacobi4_top(N, q);
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = w * w + x * x - y * y - z * z;
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = w * w - x * x + y * y - z * z;
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = w * w - x * x - y * y + z * z;
+}
+
+// phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One warp per
+// (instance, rotation); the item partials are summed in a fixed order.
+__global__ void k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
+  const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
+  const InstDev& D = insts[inst];
+  if (a >= *D.n_found) return;
+  const int lane = threadIdx.x;
+  double s[10];
+  for (int t = 0; t < 10; ++t) s[t] = 0.0;
+  const double* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
+  for (int it = lane; it < D.n_items; it += 32)
+    for (int t = 0; t < 10; ++t) s[t] += base[(int64_t)it * D.k * 10 + t];
+  for (int t = 0; t < 10; ++t) s[t] = warp_sum_d(s[t]);
+  if (lane != 0) return;
+  DevRot& R = D.rot[a];
+  double out[9];
+  uint32_t cnt = (uint32_t)s[9];
+  if (cnt == 0) {
+    const double* fb = phase == 0 ? R.R_vote : R.R_init;
+    for (int t = 0; t < 9; ++t) out[t] = fb[t];
+  } else {
+    horn_rotation(s, out);
+  }
+  if (phase == 0) {
+    for (int t = 0; t < 9; ++t) {
+      R.R_init[t] = out[t];
+      R.R_init_f[t] = (float)out[t];
+    }
+    R.n_vote_set = cnt;
+  } else {
+    for (int t = 0; t < 9; ++t) R.R[t] = out[t];
+    R.n_inliers = cnt;
+    R.n_degenerate = *D.n_deg;
+  }
+}
+
+// Peaks of a caller grid as (row, col) pairs and counts (stage entry point).
+__global__ void k_write_peaks(const InstDev* __restrict__ insts, int32_t* cells, uint32_t* counts,
+                              int32_t* n_found) {
+  const InstDev& D = insts[0];
+  int found = 0;
+  for (int a = 0; a < D.k; ++a) {
+    unsigned long long key = D.peak_key[a];
+    if (!key) break;
+    uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+    cells[2 * a] = idx / D.G;
+    cells[2 * a + 1] = idx % D.G;
+    counts[a] = (uint32_t)(key >> 32);
+    ++found;
+  }
+  *n_found = found;
+}
+
+}  // namespace
+
+void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, int32_t* n_found,
+                        cudaStream_t st) {
+  k_write_peaks<<<1, 1, 0, st>>>(insts, cells, counts, n_found);
+  launches_add(1);
+}
+
+void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
+                        cudaStream_t st) {
+  k_grid_reduce<<<n_items, 256, 0, st>>>(items, insts);
+  launches_add(1);
+}
+
+void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,
+                      cudaStream_t st) {
+  k_nms_round<<<n_items, 256, 0, st>>>(items, insts, round);
+  launches_add(1);
+}
+
+void launch_finalize_peaks(const InstDev* insts, int m, cudaStream_t st) {
+  k_finalize_peaks<<<(m + 127) / 128, 128, 0, st>>>(insts, m);
+  launches_add(1);
+}
+
+void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                       int max_J, cudaStream_t st) {
+  size_t smem = (size_t)max_k * max_J * sizeof(uint32_t);
+  static size_t attr = 48 * 1024;
+  if (smem > attr) {
+    cudaFuncSetAttribute(k_angle_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = smem;
+  }
+  k_angle_vote<<<n_items, kStreamThreads, smem, st>>>(items, insts, max_J);
+  launches_add(1);
+}
+
+void launch_angle_peak(const InstDev* insts, int m, int max_k, cudaStream_t st) {
+  k_angle_peak<<<m * max_k, 256, 0, st>>>(insts, max_k);
+  launches_add(1);
+}
+
+void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                         cudaStream_t st) {
+  if (max_k <= 1)
+    k_vote_set_sum<1><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else if (max_k <= 2)
+    k_vote_set_sum<2><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else if (max_k <= 4)
+    k_vote_set_sum<4><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else
+    k_vote_set_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  launches_add(1);
+}
+
+void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st) {
+  k_kabsch<<<m * max_k, 32, 0, st>>>(insts, max_k, phase);
+  launches_add(1);
+}
+
+void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                      cudaStream_t st) {
+  if (max_k <= 1)
+    k_label_sum<1><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else if (max_k <= 2)
+    k_label_sum<2><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else if (max_k <= 4)
+    k_label_sum<4><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  else
+    k_label_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+  launches_add(1);
+}
+
+}  // namespace sprot

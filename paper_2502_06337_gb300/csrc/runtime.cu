@@ -1,0 +1,682 @@
+// Host runtime of libsprot: validation, planning, device workspaces and the launch sequence
+// behind the C ABI of include/sprot.h.
+//
+// A call (single problem or batch) is planned on the host: each instance gets its accumulator
+// side G, row bands that fit the 227 KB shared-memory tile and carry equal expected vote
+// work, circle slices, and per-pair work items. The plan becomes three work tables and an
+// instance table, copied to the device in one transfer; the kernels then run on the caller's
+// stream in a fixed order with no host round trip until the final results copy.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "sprot_internal.h"
+
+namespace sprot {
+
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launches_add(uint64_t k) { return g_launches.fetch_add(k) + k; }
+
+// Axis-vote kernel timing (measurement only): events around each launch, read after the
+// launching call has synchronised its stream.
+static std::atomic<int> g_timing{0};
+static std::mutex g_timing_mu;
+static double g_vote_ms = 0.0;
+static uint64_t g_vote_launches = 0;
+
+struct VoteTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  explicit VoteTimer(cudaStream_t st) {
+    if (!g_timing.load()) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecord(a, st);
+  }
+  void stop(cudaStream_t st) {
+    if (a) cudaEventRecord(b, st);
+  }
+  // call after the stream has been synchronised
+  void collect() {
+    if (!a) return;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+      std::lock_guard<std::mutex> g(g_timing_mu);
+      g_vote_ms += ms;
+      g_vote_launches += 1;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    a = b = nullptr;
+  }
+  ~VoteTimer() { collect(); }
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+int sm_count(int dev) {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (v <= 0) v = 1;
+  cache[dev] = v;
+  return v;
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, int k) {
+  if (!P || !Q || !p) return SPROT_E_INVAL;
+  if (n < 1 || n > (int64_t)1 << 31) return SPROT_E_INVAL;
+  int G = p->grid;
+  if (G != 0 && (!is_pow2(G) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)) return SPROT_E_INVAL;
+  if (p->angle_bins < 2 || p->angle_bins > SPROT_MAX_ANGLE_BINS) return SPROT_E_INVAL;
+  if (k < 1 || k > SPROT_MAX_K) return SPROT_E_INVAL;
+  if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return SPROT_E_INVAL;
+  if (!(p->nms_deg >= 0.f) || !std::isfinite(p->nms_deg)) return SPROT_E_INVAL;
+  if (p->gate_window < -1 || p->angle_window < 0) return SPROT_E_INVAL;
+  return SPROT_OK;
+}
+
+// Row bands of a G x G accumulator. Each band must fit the shared tile (G/2 words per row);
+// band edges split the expected work evenly: random great circles cross the plane with
+// density proportional to 2 / (1 + u^2 + v^2) (the stereographic length element over the
+// uniform density of the sphere), whose integral across a row is
+// (4 / a) atan(1 / a), a = sqrt(1 + v^2).
+void plan_bands(int G, int* n_bands, int32_t* row0) {
+  const int cap = kMaxSmemBytes / (G / 2 * 4);
+  std::vector<double> cum(G + 1, 0.0);
+  for (int r = 0; r < G; ++r) {
+    double v = -1.0 + (2.0 * r + 1.0) / G, a = std::sqrt(1.0 + v * v);
+    cum[r + 1] = cum[r] + 4.0 / a * std::atan(1.0 / a);
+  }
+  for (int T = (G + cap - 1) / cap; T <= kMaxBands; ++T) {
+    std::vector<int32_t> e(T + 1);
+    e[0] = 0;
+    e[T] = G;
+    for (int b = 1; b < T; ++b) {
+      double target = cum[G] * b / T;
+      int r = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+      e[b] = std::min(std::max(r, e[b - 1] + 1), G - (T - b));
+    }
+    bool fits = true;
+    for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= cap;
+    if (fits) {
+      *n_bands = T;
+      for (int b = 0; b <= T; ++b) row0[b] = e[b];
+      return;
+    }
+  }
+  // unreachable for G <= 2048 (cap >= 56 rows)
+  *n_bands = 0;
+}
+
+struct InstPlan {
+  int64_t n;
+  int G, J, k, w, window;
+  float tau;
+  double cos_nms;
+  int T, S;
+  int32_t row0[kMaxBands + 1];
+  int chunk, n_items, item0;
+  // arena offsets
+  size_t o_partial, o_grid, o_bins, o_msum, o_labels, o_vote_set, o_P, o_Q, o_mask;
+  size_t o_peak, o_hist, o_ndeg;   // zero region
+  size_t o_nfound, o_rot;          // result region
+};
+
+struct Workspace {
+  std::mutex mu;
+  int device = 0;
+  char* dev = nullptr;
+  size_t dev_cap = 0;
+  char* host = nullptr;  // pinned
+  size_t host_cap = 0;
+  ~Workspace() {
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+  }
+  int reserve(size_t dbytes, size_t hbytes) {
+    if (dbytes > dev_cap) {
+      size_t want = std::max(dbytes, dev_cap + dev_cap / 2);
+      if (dev) cudaFree(dev);
+      dev = nullptr;
+      dev_cap = 0;
+      if (cudaMalloc(&dev, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&dev, dbytes) != cudaSuccess) {
+          cudaGetLastError();
+          dev = nullptr;
+          return SPROT_E_NOMEM;
+        }
+        want = dbytes;
+      }
+      dev_cap = want;
+    }
+    if (hbytes > host_cap) {
+      if (host) cudaFreeHost(host);
+      host = nullptr;
+      host_cap = 0;
+      if (cudaMallocHost(&host, hbytes) != cudaSuccess) {
+        cudaGetLastError();
+        host = nullptr;
+        return SPROT_E_NOMEM;
+      }
+      host_cap = hbytes;
+    }
+    return SPROT_OK;
+  }
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Workspace>> g_ws;
+
+Workspace* workspace_for(cudaStream_t st, int* status) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    *status = SPROT_E_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  auto& slot = g_ws[{dev, st}];
+  if (!slot) {
+    slot.reset(new Workspace());
+    slot->device = dev;
+  }
+  *status = SPROT_OK;
+  return slot.get();
+}
+
+int stream_chunk(int64_t n) {
+  int64_t c = (n + 599) / 600;
+  c = (c + 255) / 256 * 256;
+  return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
+}
+
+}  // namespace
+
+size_t problem_footprint(int64_t n, int G, int J, int k) {
+  int T = 0;
+  int32_t row0[kMaxBands + 1];
+  plan_bands(G, &T, row0);
+  int64_t S = std::max<int64_t>((n + 32767) / 32768, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
+  int64_t items = (n + stream_chunk(n) - 1) / stream_chunk(n);
+  return align_up((size_t)S * G * (G / 2) * 4) + align_up((size_t)G * G * 4) +
+         align_up((size_t)k * n * 2) + align_up((size_t)2 * items * k * 80) + align_up((size_t)n * 4) +
+         align_up((size_t)k * J * 4) + align_up(sizeof(DevRot) * k) + 4096;
+}
+
+// Solves a batch of problems on stream st. Every Problem must be validated already.
+int solve(std::vector<Problem>& probs, cudaStream_t st) {
+  const int m = (int)probs.size();
+  int status = SPROT_OK;
+  Workspace* ws = workspace_for(st, &status);
+  if (!ws) return status;
+  std::lock_guard<std::mutex> lock(ws->mu);
+  const int nsm = sm_count(ws->device);
+
+  // ---- plan ---------------------------------------------------------------------------
+  std::vector<InstPlan> plan(m);
+  std::vector<VoteItem> vitems;
+  std::vector<ReduceItem> ritems;
+  std::vector<StreamItem> sitems;
+  int max_k = 1, max_J = 2;
+  for (int i = 0; i < m; ++i) {
+    const Problem& pb = probs[i];
+    InstPlan& ip = plan[i];
+    ip.n = pb.n;
+    ip.G = pb.prm.grid ? pb.prm.grid : sprot_autotune_grid(pb.n);
+    ip.J = pb.prm.angle_bins;
+    ip.k = pb.k;
+    ip.w = pb.prm.gate_window;
+    ip.window = pb.prm.angle_window;
+    ip.tau = (float)pb.prm.tau;
+    ip.cos_nms = std::cos((double)pb.prm.nms_deg * 3.14159265358979323846 / 180.0);
+    plan_bands(ip.G, &ip.T, ip.row0);
+    if (ip.T <= 0) return SPROT_E_INVAL;
+    int64_t s_min = (pb.n + kMaxSliceCircles - 1) / kMaxSliceCircles;
+    int64_t s = (m == 1) ? std::max<int64_t>(1, nsm / ip.T) : (pb.n + 32767) / 32768;
+    s = std::min<int64_t>(s, std::max<int64_t>(1, (pb.n + 511) / 512));
+    ip.S = (int)std::max(s, s_min);
+    for (int sl = 0; sl < ip.S; ++sl) {
+      int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
+      for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
+    }
+    int64_t words = (int64_t)ip.G * (ip.G / 2);
+    for (int64_t w0 = 0; w0 < words; w0 += 1024)
+      ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+    ip.chunk = stream_chunk(pb.n);
+    ip.item0 = (int)sitems.size();
+    for (int64_t a = 0; a < pb.n; a += ip.chunk)
+      sitems.push_back(StreamItem{i, 0, a, std::min<int64_t>(a + ip.chunk, pb.n)});
+    ip.n_items = (int)sitems.size() - ip.item0;
+    max_k = std::max(max_k, ip.k);
+    max_J = std::max(max_J, ip.J);
+  }
+  // Longest vote items first, so the persistent CTAs finish together.
+  std::stable_sort(vitems.begin(), vitems.end(), [&](const VoteItem& a, const VoteItem& b) {
+    double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
+    double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
+    return wa > wb;
+  });
+
+  // ---- layout -------------------------------------------------------------------------
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t o_inst = take(sizeof(InstDev) * m);
+  const size_t o_vit = take(sizeof(VoteItem) * vitems.size());
+  const size_t o_rit = take(sizeof(ReduceItem) * ritems.size());
+  const size_t o_sit = take(sizeof(StreamItem) * sitems.size());
+  const size_t header_end = off;
+  const size_t o_zero = off;
+  const size_t o_counter = take(sizeof(int));
+  for (auto& ip : plan) {
+    ip.o_peak = take(sizeof(unsigned long long) * ip.k);
+    ip.o_hist = take(sizeof(uint32_t) * ip.k * ip.J);
+    ip.o_ndeg = take(sizeof(uint32_t));
+  }
+  const size_t zero_end = off;
+  const size_t o_res = off;
+  for (auto& ip : plan) {
+    ip.o_nfound = take(sizeof(int32_t));
+    ip.o_rot = take(sizeof(DevRot) * ip.k);
+  }
+  const size_t res_end = off;
+  for (int i = 0; i < m; ++i) {
+    InstPlan& ip = plan[i];
+    const Problem& pb = probs[i];
+    ip.o_partial = take((size_t)ip.S * ip.G * (ip.G / 2) * 4);
+    ip.o_grid = take((size_t)ip.G * ip.G * 4);
+    ip.o_bins = take((size_t)ip.k * ip.n * 2);
+    ip.o_msum = take((size_t)2 * ip.n_items * ip.k * 10 * 8);
+    ip.o_labels = (pb.labels && !pb.host_io) ? 0 : take((size_t)ip.n * 4);
+    ip.o_vote_set = 0;
+    ip.o_P = pb.host_io ? take((size_t)ip.n * 12) : 0;
+    ip.o_Q = pb.host_io ? take((size_t)ip.n * 12) : 0;
+    ip.o_mask = (pb.host_io && pb.mask) ? take((size_t)ip.n) : 0;
+  }
+  const size_t dev_bytes = off;
+  const size_t host_bytes = align_up(header_end) + (res_end - o_res);
+  status = ws->reserve(dev_bytes, host_bytes);
+  if (status != SPROT_OK) return status;
+  char* D = ws->dev;
+  char* H = ws->host;
+
+  // ---- tables -------------------------------------------------------------------------
+  InstDev* hid = reinterpret_cast<InstDev*>(H + o_inst);
+  for (int i = 0; i < m; ++i) {
+    const InstPlan& ip = plan[i];
+    const Problem& pb = probs[i];
+    InstDev& d = hid[i];
+    std::memset(&d, 0, sizeof(d));
+    d.P = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_P) : pb.P;
+    d.Q = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_Q) : pb.Q;
+    d.n = ip.n;
+    d.G = ip.G;
+    d.J = ip.J;
+    d.k = ip.k;
+    d.w = ip.w;
+    d.window = ip.window;
+    d.n_bands = ip.T;
+    d.S = ip.S;
+    d.tau = ip.tau;
+    d.cos_nms = ip.cos_nms;
+    for (int b = 0; b <= ip.T; ++b) d.band_row0[b] = ip.row0[b];
+    d.partial = reinterpret_cast<uint32_t*>(D + ip.o_partial);
+    d.grid = (pb.dbg && pb.dbg->grid) ? pb.dbg->grid : reinterpret_cast<uint32_t*>(D + ip.o_grid);
+    d.peak_key = reinterpret_cast<unsigned long long*>(D + ip.o_peak);
+    d.hist = (pb.dbg && pb.dbg->hist) ? nullptr : reinterpret_cast<uint32_t*>(D + ip.o_hist);
+    d.bins = (pb.dbg && pb.dbg->bins) ? pb.dbg->bins : reinterpret_cast<int16_t*>(D + ip.o_bins);
+    d.msum = reinterpret_cast<double*>(D + ip.o_msum);
+    d.item0 = ip.item0;
+    d.n_items = ip.n_items;
+    d.n_found = reinterpret_cast<int32_t*>(D + ip.o_nfound);
+    d.n_deg = reinterpret_cast<uint32_t*>(D + ip.o_ndeg);
+    d.rot = reinterpret_cast<DevRot*>(D + ip.o_rot);
+    d.labels = (pb.labels && !pb.host_io) ? pb.labels : reinterpret_cast<int32_t*>(D + ip.o_labels);
+    d.vote_set = pb.dbg ? pb.dbg->vote_set : nullptr;
+    d.mask = pb.mask ? (pb.host_io ? reinterpret_cast<uint8_t*>(D + ip.o_mask) : pb.mask) : nullptr;
+  }
+  // A caller-supplied histogram buffer is zeroed and used in place.
+  for (int i = 0; i < m; ++i)
+    if (probs[i].dbg && probs[i].dbg->hist) hid[i].hist = probs[i].dbg->hist;
+  std::memcpy(H + o_vit, vitems.data(), sizeof(VoteItem) * vitems.size());
+  std::memcpy(H + o_rit, ritems.data(), sizeof(ReduceItem) * ritems.size());
+  std::memcpy(H + o_sit, sitems.data(), sizeof(StreamItem) * sitems.size());
+
+  // ---- launches -----------------------------------------------------------------------
+  auto ck = [](cudaError_t e) { return e == cudaSuccess; };
+  bool ok = true;
+  ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
+  ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
+  for (int i = 0; i < m; ++i) {
+    const Problem& pb = probs[i];
+    if (pb.dbg && pb.dbg->hist)
+      ok &= ck(cudaMemsetAsync(pb.dbg->hist, 0, sizeof(uint32_t) * plan[i].k * plan[i].J, st));
+    if (pb.host_io) {
+      ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
+      ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
+    }
+  }
+  if (!ok) return SPROT_E_CUDA;
+  const InstDev* dinst = reinterpret_cast<const InstDev*>(D + o_inst);
+  const VoteItem* dvit = reinterpret_cast<const VoteItem*>(D + o_vit);
+  const ReduceItem* drit = reinterpret_cast<const ReduceItem*>(D + o_rit);
+  const StreamItem* dsit = reinterpret_cast<const StreamItem*>(D + o_sit);
+  int* dcounter = reinterpret_cast<int*>(D + o_counter);
+  int smem = 0;
+  for (auto& ip : plan) {
+    int rows = 0;
+    for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+    smem = std::max(smem, rows * (ip.G / 2) * 4);
+  }
+  int ctas = (int)std::min<size_t>(vitems.size(), (size_t)nsm);
+  VoteTimer vt(st);
+  launch_axis_vote(dvit, (int)vitems.size(), dinst, dcounter, ctas, smem, st);
+  vt.stop(st);
+  launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
+  for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
+  launch_finalize_peaks(dinst, m, st);
+  launch_angle_vote(dsit, (int)sitems.size(), dinst, max_k, max_J, st);
+  launch_angle_peak(dinst, m, max_k, st);
+  launch_vote_set_sum(dsit, (int)sitems.size(), dinst, max_k, st);
+  launch_kabsch(dinst, m, max_k, 0, st);
+  launch_label_sum(dsit, (int)sitems.size(), dinst, max_k, st);
+  launch_kabsch(dinst, m, max_k, 1, st);
+  if (!ck(cudaGetLastError())) return SPROT_E_CUDA;
+
+  // ---- results ------------------------------------------------------------------------
+  char* Hres = H + align_up(header_end);
+  ok &= ck(cudaMemcpyAsync(Hres, D + o_res, res_end - o_res, cudaMemcpyDeviceToHost, st));
+  for (int i = 0; i < m; ++i) {
+    const Problem& pb = probs[i];
+    if (!pb.host_io) continue;
+    if (pb.labels)
+      ok &= ck(cudaMemcpyAsync(pb.labels, D + plan[i].o_labels, (size_t)pb.n * 4,
+                               cudaMemcpyDeviceToHost, st));
+    if (pb.mask)
+      ok &= ck(cudaMemcpyAsync(pb.mask, D + plan[i].o_mask, (size_t)pb.n, cudaMemcpyDeviceToHost, st));
+  }
+  if (!ok || !ck(cudaStreamSynchronize(st))) return SPROT_E_CUDA;
+  vt.collect();
+  int worst = SPROT_OK;
+  for (int i = 0; i < m; ++i) {
+    const InstPlan& ip = plan[i];
+    const Problem& pb = probs[i];
+    int32_t nf = *reinterpret_cast<int32_t*>(Hres + (ip.o_nfound - o_res));
+    const DevRot* dr = reinterpret_cast<const DevRot*>(Hres + (ip.o_rot - o_res));
+    if (pb.n_found) *pb.n_found = nf;
+    for (int a = 0; a < nf; ++a) {
+      sprot_rotation& o = pb.out[a];
+      const DevRot& r = dr[a];
+      std::memcpy(o.R, r.R, sizeof(o.R));
+      std::memcpy(o.R_init, r.R_init, sizeof(o.R_init));
+      std::memcpy(o.R_vote, r.R_vote, sizeof(o.R_vote));
+      std::memcpy(o.axis, r.axis, sizeof(o.axis));
+      o.theta = r.theta;
+      o.cell_row = r.cell_row;
+      o.cell_col = r.cell_col;
+      o.angle_bin = r.angle_bin;
+      o.axis_votes = r.axis_votes;
+      o.angle_votes = r.angle_votes;
+      o.n_vote_set = r.n_vote_set;
+      o.n_inliers = r.n_inliers;
+      o.n_degenerate = r.n_degenerate;
+    }
+    if (nf == 0) worst = SPROT_E_NOAXIS;
+    probs[i].prm.grid = ip.G;
+  }
+  return m == 1 ? worst : SPROT_OK;
+}
+
+// Accumulator only (stage entry point): vote + slice reduction into a caller grid.
+int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* grid,
+                   cudaStream_t st) {
+  int status = SPROT_OK;
+  Workspace* ws = workspace_for(st, &status);
+  if (!ws) return status;
+  std::lock_guard<std::mutex> lock(ws->mu);
+  const int nsm = sm_count(ws->device);
+  InstPlan ip{};
+  plan_bands(G, &ip.T, ip.row0);
+  int64_t s = std::max<int64_t>(1, nsm / ip.T);
+  s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
+  ip.S = (int)std::max<int64_t>(s, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
+  std::vector<VoteItem> vit;
+  for (int sl = 0; sl < ip.S; ++sl)
+    for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
+  std::vector<ReduceItem> rit;
+  int64_t words = (int64_t)G * (G / 2);
+  for (int64_t w0 = 0; w0 < words; w0 += 1024) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
+  size_t o_inst = take(sizeof(InstDev)), o_vit = take(sizeof(VoteItem) * vit.size()),
+         o_rit = take(sizeof(ReduceItem) * rit.size());
+  size_t hdr = off;
+  size_t o_zero = take(sizeof(int)), o_peak = take(8);
+  size_t zend = off;
+  size_t o_part = take((size_t)ip.S * G * (G / 2) * 4);
+  status = ws->reserve(off, hdr);
+  if (status != SPROT_OK) return status;
+  char* D = ws->dev;
+  char* H = ws->host;
+  InstDev& d = *reinterpret_cast<InstDev*>(H + o_inst);
+  std::memset(&d, 0, sizeof(d));
+  d.P = P;
+  d.Q = Q;
+  d.n = n;
+  d.G = G;
+  d.k = 1;
+  d.n_bands = ip.T;
+  d.S = ip.S;
+  for (int b = 0; b <= ip.T; ++b) d.band_row0[b] = ip.row0[b];
+  d.partial = reinterpret_cast<uint32_t*>(D + o_part);
+  d.grid = grid;
+  d.peak_key = reinterpret_cast<unsigned long long*>(D + o_peak);
+  std::memcpy(H + o_vit, vit.data(), sizeof(VoteItem) * vit.size());
+  std::memcpy(H + o_rit, rit.data(), sizeof(ReduceItem) * rit.size());
+  if (cudaMemcpyAsync(D, H, hdr, cudaMemcpyHostToDevice, st) != cudaSuccess) return SPROT_E_CUDA;
+  if (cudaMemsetAsync(D + o_zero, 0, zend - o_zero, st) != cudaSuccess) return SPROT_E_CUDA;
+  int rows = 0;
+  for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+  VoteTimer vt(st);
+  launch_axis_vote(reinterpret_cast<VoteItem*>(D + o_vit), (int)vit.size(),
+                   reinterpret_cast<InstDev*>(D + o_inst), reinterpret_cast<int*>(D + o_zero),
+                   (int)std::min<size_t>(vit.size(), (size_t)nsm), rows * (G / 2) * 4, st);
+  vt.stop(st);
+  launch_grid_reduce(reinterpret_cast<ReduceItem*>(D + o_rit), (int)rit.size(),
+                     reinterpret_cast<InstDev*>(D + o_inst), st);
+  if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
+  // the host staging is reused by the next call: wait for the copy to have been consumed
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPROT_E_CUDA;
+  return SPROT_OK;
+}
+
+// Greedy top-k with suppression on a caller grid (stage entry point).
+int select_peaks(const uint32_t* grid, int G, int k, float nms_deg, int32_t* cells,
+                 uint32_t* counts, int32_t* n_found, cudaStream_t st) {
+  int status = SPROT_OK;
+  Workspace* ws = workspace_for(st, &status);
+  if (!ws) return status;
+  std::lock_guard<std::mutex> lock(ws->mu);
+  std::vector<ReduceItem> rit;
+  int64_t words = (int64_t)G * (G / 2);
+  for (int64_t w0 = 0; w0 < words; w0 += 1024) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
+  size_t o_inst = take(sizeof(InstDev)), o_rit = take(sizeof(ReduceItem) * rit.size());
+  size_t hdr = off;
+  size_t o_peak = take(8 * (size_t)k);
+  status = ws->reserve(off, hdr);
+  if (status != SPROT_OK) return status;
+  char* D = ws->dev;
+  char* H = ws->host;
+  InstDev& d = *reinterpret_cast<InstDev*>(H + o_inst);
+  std::memset(&d, 0, sizeof(d));
+  d.G = G;
+  d.k = k;
+  d.cos_nms = std::cos((double)nms_deg * 3.14159265358979323846 / 180.0);
+  d.grid = const_cast<uint32_t*>(grid);
+  d.peak_key = reinterpret_cast<unsigned long long*>(D + o_peak);
+  std::memcpy(H + o_rit, rit.data(), sizeof(ReduceItem) * rit.size());
+  if (cudaMemcpyAsync(D, H, hdr, cudaMemcpyHostToDevice, st) != cudaSuccess) return SPROT_E_CUDA;
+  if (cudaMemsetAsync(D + o_peak, 0, 8 * (size_t)k, st) != cudaSuccess) return SPROT_E_CUDA;
+  const InstDev* di = reinterpret_cast<const InstDev*>(D + o_inst);
+  for (int r = 0; r < k; ++r)
+    launch_nms_round(reinterpret_cast<const ReduceItem*>(D + o_rit), (int)rit.size(), di, r, st);
+  launch_write_peaks(di, cells, counts, n_found, st);
+  if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPROT_E_CUDA;
+  return SPROT_OK;
+}
+
+}  // namespace sprot
+
+using namespace sprot;
+
+extern "C" {
+
+void sprot_default_params(sprot_params* p) {
+  if (!p) return;
+  p->grid = 256;
+  p->angle_bins = 360;
+  p->k = 1;
+  p->nms_deg = 2.0f;
+  p->gate_window = 1;
+  p->angle_window = 1;
+  p->tau = 0.05;
+  p->flags = 0;
+}
+
+const char* sprot_status_string(int s) {
+  switch (s) {
+    case SPROT_OK: return "ok";
+    case SPROT_E_INVAL: return "invalid argument";
+    case SPROT_E_NOMEM: return "out of memory or over budget";
+    case SPROT_E_CUDA: return "CUDA error";
+    case SPROT_E_TIMEOUT: return "timed out";
+    case SPROT_E_NOAXIS: return "no axis: every accumulator cell is zero";
+    case SPROT_E_UNIMPL: return "not implemented";
+    case SPROT_E_BUSY: return "server busy or stopping";
+    default: return "unknown status";
+  }
+}
+
+int32_t sprot_autotune_grid(int64_t n) {
+  if (n < 3000) return 128;
+  if (n < 300000) return 256;
+  return 512;
+}
+
+int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n, const sprot_params* params,
+                                sprot_rotation* out, int32_t* n_found, int32_t* labels,
+                                const sprot_debug* dbg, void* stream) {
+  if (!params || !out) return SPROT_E_INVAL;
+  int st = validate(P, Q, n, params, params->k);
+  if (st != SPROT_OK) return st;
+  bool host = (params->flags & SPROT_HOST_PTRS) != 0;
+  if (host && dbg) return SPROT_E_INVAL;
+  std::vector<Problem> pb(1);
+  pb[0] = Problem{P, Q, n, *params, params->k, host, out, n_found, labels, nullptr, dbg};
+  if (pb[0].prm.grid == 0) pb[0].prm.grid = sprot_autotune_grid(n);
+  return solve(pb, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int sprot_estimate_rotations_k(const float* P, const float* Q, int64_t n, const sprot_params* params,
+                               sprot_rotation* out, int32_t* n_found, int32_t* labels, void* stream) {
+  return sprot_estimate_rotations_ex(P, Q, n, params, out, n_found, labels, nullptr, stream);
+}
+
+int sprot_estimate_rotation(const float* P, const float* Q, int64_t n, const sprot_params* params,
+                            sprot_rotation* out, uint8_t* inlier_mask, void* stream) {
+  if (!params || !out) return SPROT_E_INVAL;
+  sprot_params p1 = *params;
+  p1.k = 1;
+  int st = validate(P, Q, n, &p1, 1);
+  if (st != SPROT_OK) return st;
+  bool host = (p1.flags & SPROT_HOST_PTRS) != 0;
+  int32_t nf = 0;
+  std::vector<Problem> pb(1);
+  pb[0] = Problem{P, Q, n, p1, 1, host, out, &nf, nullptr, inlier_mask, nullptr};
+  if (pb[0].prm.grid == 0) pb[0].prm.grid = sprot_autotune_grid(n);
+  return solve(pb, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t G, uint32_t* grid, void* stream) {
+  if (!P || !Q || !grid || n < 1 || !is_pow2(G) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)
+    return SPROT_E_INVAL;
+  return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int sprot_select_peaks(const uint32_t* grid, int32_t G, int32_t k, float nms_deg, int32_t* cells,
+                       uint32_t* counts, int32_t* n_found, void* stream) {
+  if (!grid || !cells || !counts || !n_found || !is_pow2(G) || G < SPROT_MIN_GRID ||
+      G > SPROT_MAX_GRID || k < 1 || k > SPROT_MAX_K || !(nms_deg >= 0.f))
+    return SPROT_E_INVAL;
+  return select_peaks(grid, G, k, nms_deg, cells, counts, n_found, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream) {
+  if (!inst || m < 1) return SPROT_E_INVAL;
+  std::vector<Problem> pb((size_t)m);
+  for (int64_t i = 0; i < m; ++i) {
+    const sprot_instance& x = inst[i];
+    int st = validate(x.P, x.Q, x.n, &x.params, x.params.k);
+    if (st != SPROT_OK || !x.out || (x.params.flags & SPROT_HOST_PTRS)) return SPROT_E_INVAL;
+    pb[i] = Problem{x.P, x.Q, x.n, x.params, x.params.k, false, x.out, x.n_found, x.labels, nullptr, nullptr};
+    if (pb[i].prm.grid == 0) pb[i].prm.grid = sprot_autotune_grid(x.n);
+  }
+  int st = solve(pb, reinterpret_cast<cudaStream_t>(stream));
+  if (st == SPROT_OK)
+    for (int64_t i = 0; i < m; ++i) inst[i].params.grid = pb[i].prm.grid;
+  return st;
+}
+
+void sprot_release_workspaces(void) {
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  g_ws.clear();
+}
+
+uint64_t sprot_kernel_launch_count(void) { return g_launches.load(); }
+
+void sprot_kernel_timing(int enable) {
+  std::lock_guard<std::mutex> g(g_timing_mu);
+  g_timing.store(enable ? 1 : 0);
+  if (enable) {
+    g_vote_ms = 0.0;
+    g_vote_launches = 0;
+  }
+}
+
+void sprot_kernel_timing_read(double* vote_ms, uint64_t* vote_launches) {
+  std::lock_guard<std::mutex> g(g_timing_mu);
+  if (vote_ms) *vote_ms = g_vote_ms;
+  if (vote_launches) *vote_launches = g_vote_launches;
+}
+
+int sprot_probe_smem_atomic_rate(int32_t iters, double* rate, void* stream) {
+  if (!rate || iters < 1) return SPROT_E_INVAL;
+  double r = probe_smem_atomics(iters, reinterpret_cast<cudaStream_t>(stream));
+  if (r <= 0) return SPROT_E_CUDA;
+  *rate = r;
+  return SPROT_OK;
+}
+
+}  // extern "C"

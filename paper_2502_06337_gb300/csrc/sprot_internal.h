@@ -1,0 +1,119 @@
+// Internal structures shared by the CUDA translation units of libsprot (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/sprot.h"
+
+namespace sprot {
+
+constexpr int kMaxK = SPROT_MAX_K;
+constexpr int kMaxBands = 48;        // row bands of one accumulator (G = 2048 needs 37)
+constexpr int kVoteThreads = 1024;   // threads of the axis-vote CTA
+constexpr int kStreamThreads = 256;  // threads of the per-pair kernels
+constexpr int kStreamChunk = 8192;   // pairs per per-pair work item
+constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // tile; leaves room for static shared
+constexpr int kMaxSliceCircles = 65535;  // u16 tile counters: at most this many circles/slice
+
+// Device-side result of one rotation; mirrors sprot_rotation plus internals.
+struct DevRot {
+  double R[9];
+  double R_init[9];
+  double R_vote[9];
+  double axis[3];
+  double theta;
+  float r_cell[3];   // canonical (r_z <= 0) cell axis in float32, used by the angle vote
+  float R_init_f[9]; // R_init rounded to float32, used by the residual labels
+  int32_t cell_row, cell_col, angle_bin;
+  uint32_t axis_votes, angle_votes, n_vote_set, n_inliers, n_degenerate;
+};
+
+// One problem of a (possibly single-element) batch, as the kernels see it.
+struct InstDev {
+  const float* P;
+  const float* Q;
+  int64_t n;
+  int32_t G, J, k, w, window;
+  int32_t n_bands, S;            // row bands and circle slices of the axis vote
+  float tau;
+  double cos_nms;                // cosine of the suppression radius between axis lines
+  int32_t band_row0[kMaxBands + 1];
+  // workspace
+  uint32_t* partial;             // [S][G][G/2] u16 pairs (col c and c + G/2 share a word)
+  uint32_t* grid;                // [G][G]
+  unsigned long long* peak_key;  // [k] packed (count, ~index) maxima
+  uint32_t* hist;                // [k][J]
+  int16_t* bins;                 // [k][n]
+  double* msum;                  // [2][n_items][k][10]: 9 sums of q p^T and a count
+  int32_t item0, n_items;        // this instance's per-pair work items
+  int32_t* n_found;              // device int
+  uint32_t* n_deg;               // device count of degenerate pairs
+  DevRot* rot;                   // [k]
+  int32_t* labels;               // [n] (caller or workspace)
+  uint8_t* vote_set;             // [k][n] or null
+  uint8_t* mask;                 // [n] 1 = labelled inlier, or null
+};
+
+struct VoteItem {
+  int32_t inst, band, slice, pad;
+  int64_t c0, c1;  // circle range [c0, c1)
+};
+
+struct StreamItem {
+  int32_t inst, pad;
+  int64_t i0, i1;
+};
+
+struct ReduceItem {
+  int32_t inst, pad;
+  int64_t w0, w1;  // packed-word range of the grid
+};
+
+// One problem of a solve() call. Pointers are device pointers unless host_io is set.
+struct Problem {
+  const float* P;
+  const float* Q;
+  int64_t n;
+  sprot_params prm;
+  int k;
+  bool host_io;
+  sprot_rotation* out;    // host, k entries
+  int32_t* n_found;       // host
+  int32_t* labels;        // per-pair labels (device, or host if host_io), may be null
+  uint8_t* mask;          // per-pair inlier mask (device, or host if host_io), may be null
+  const sprot_debug* dbg; // device debug outputs, may be null
+};
+
+// Solves the problems (validated by the caller) with one launch sequence on st and waits for
+// the results. Returns SPROT_OK, or for a single problem SPROT_E_NOAXIS when it has no peak.
+int solve(std::vector<Problem>& probs, cudaStream_t st);
+
+// Device bytes one problem occupies in a solve() workspace (inputs excluded).
+size_t problem_footprint(int64_t n, int G, int J, int k);
+
+// ---- launchers (kernels.cu) ------------------------------------------------------------
+void launch_axis_vote(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
+                      int grid_ctas, int smem_bytes, cudaStream_t st);
+void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
+                        cudaStream_t st);
+void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,
+                      cudaStream_t st);
+void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, int32_t* n_found,
+                        cudaStream_t st);
+void launch_finalize_peaks(const InstDev* insts, int m, cudaStream_t st);
+void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                       int max_J, cudaStream_t st);
+void launch_angle_peak(const InstDev* insts, int m, int max_k, cudaStream_t st);
+void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                         cudaStream_t st);
+void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st);
+void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
+                      cudaStream_t st);
+double probe_smem_atomics(int iters, cudaStream_t st);
+
+uint64_t launches_add(uint64_t k);
+
+}  // namespace sprot
