@@ -163,7 +163,7 @@ def test_determinism_permutation_and_swap(lib):
     a = parity.run_gpu(prob.P, prob.Q, G, 360)
     b = parity.run_gpu(prob.Q, prob.P, G, 360)
     assert np.array_equal(a["hist"][0], b["hist"][0][::-1])
-    assert oracle.rotation_error(a["rots"][0]["R"].T, b["rots"][0]["R"]) < 1e-12
+    assert parity.rot_diff(a["rots"][0]["R"].T, b["rots"][0]["R"]) < 1e-12
 
 
 def test_headline_scale(lib):
