@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -129,7 +130,7 @@ struct InstPlan {
   int G, J, k, w, window;
   float tau;
   double cos_nms;
-  int T, S;
+  int T, S, C;  // bands (banded kernel), slices, cluster size (0 = banded kernel)
   int32_t row0[kMaxBands + 1];
   int chunk, n_items, item0;
   // arena offsets
@@ -206,6 +207,53 @@ int stream_chunk(int64_t n) {
   return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
 }
 
+// Co-resident clusters of the cluster vote kernel (cached per device and cluster size).
+int active_clusters(int dev, int C, int smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto key = std::make_pair(dev, C);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int v = max_active_clusters(C, smem);
+  cache[key] = v;
+  return v;
+}
+
+// Vote layout of one instance: the cluster kernel holds the whole accumulator in one CTA or
+// one cluster; G = 2048 does not fit a cluster and falls back to row bands.
+void plan_vote(InstPlan& ip, int64_t n, bool single, int dev, int nsm) {
+  ip.C = cluster_size_for(ip.G);
+  const char* force = std::getenv("SPROT_VOTE_KERNEL");  // "banded": measurement and tests
+  if (force && std::strcmp(force, "banded") == 0) ip.C = 0;
+  const int64_t s_min = (n + kMaxSliceCircles - 1) / kMaxSliceCircles;
+  int64_t s;
+  if (ip.C == 0) {
+    plan_bands(ip.G, &ip.T, ip.row0);
+    s = single ? std::max<int64_t>(1, nsm / std::max(ip.T, 1)) : (n + 32767) / 32768;
+  } else {
+    ip.T = 1;
+    ip.row0[0] = 0;
+    ip.row0[1] = ip.G;
+    if (single) {
+      int smem = (ip.G / ip.C) * (ip.G / 2) * 4;
+      s = ip.C == 1 ? nsm : std::max(1, active_clusters(dev, ip.C, smem));
+    } else {
+      s = (n + 32767) / 32768;
+    }
+  }
+  s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
+  ip.S = (int)std::max(s, s_min);
+}
+
+struct VoteGroup {
+  int C;  // 0 = banded
+  std::vector<VoteItem> items;
+  int smem = 0;
+};
+
+int group_index(int C) { return C == 0 ? 0 : 1 + __builtin_ctz((unsigned)C); }  // 0..5
+
 }  // namespace
 
 size_t problem_footprint(int64_t n, int G, int J, int k) {
@@ -230,6 +278,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
 
   // ---- plan ---------------------------------------------------------------------------
   std::vector<InstPlan> plan(m);
+  std::vector<VoteGroup> groups(6);
   std::vector<VoteItem> vitems;
   std::vector<ReduceItem> ritems;
   std::vector<StreamItem> sitems;
@@ -245,15 +294,19 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
     ip.window = pb.prm.angle_window;
     ip.tau = (float)pb.prm.tau;
     ip.cos_nms = std::cos((double)pb.prm.nms_deg * 3.14159265358979323846 / 180.0);
-    plan_bands(ip.G, &ip.T, ip.row0);
+    plan_vote(ip, pb.n, m == 1, ws->device, nsm);
     if (ip.T <= 0) return SPROT_E_INVAL;
-    int64_t s_min = (pb.n + kMaxSliceCircles - 1) / kMaxSliceCircles;
-    int64_t s = (m == 1) ? std::max<int64_t>(1, nsm / ip.T) : (pb.n + 32767) / 32768;
-    s = std::min<int64_t>(s, std::max<int64_t>(1, (pb.n + 511) / 512));
-    ip.S = (int)std::max(s, s_min);
-    for (int sl = 0; sl < ip.S; ++sl) {
-      int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
-      for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
+    {
+      VoteGroup& vg = groups[group_index(ip.C)];
+      vg.C = ip.C;
+      int rows = 0;
+      for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+      if (ip.C > 0) rows = ip.G / ip.C;
+      vg.smem = std::max(vg.smem, rows * (ip.G / 2) * 4);
+      for (int sl = 0; sl < ip.S; ++sl) {
+        int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
+        for (int b = 0; b < ip.T; ++b) vg.items.push_back(VoteItem{i, b, sl, 0, c0, c1});
+      }
     }
     int64_t words = (int64_t)ip.G * (ip.G / 2);
     for (int64_t w0 = 0; w0 < words; w0 += 1024)
@@ -266,12 +319,18 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
     max_k = std::max(max_k, ip.k);
     max_J = std::max(max_J, ip.J);
   }
-  // Longest vote items first, so the persistent CTAs finish together.
-  std::stable_sort(vitems.begin(), vitems.end(), [&](const VoteItem& a, const VoteItem& b) {
-    double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
-    double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
-    return wa > wb;
-  });
+  // Longest vote items first within each group (persistent CTAs finish together).
+  std::vector<std::pair<int, int>> granges;  // [begin, end) of each group in vitems
+  for (auto& vg : groups) {
+    std::stable_sort(vg.items.begin(), vg.items.end(), [&](const VoteItem& a, const VoteItem& b) {
+      double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
+      double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
+      return wa > wb;
+    });
+    int b0 = (int)vitems.size();
+    vitems.insert(vitems.end(), vg.items.begin(), vg.items.end());
+    granges.push_back({b0, (int)vitems.size()});
+  }
 
   // ---- layout -------------------------------------------------------------------------
   size_t off = 0;
@@ -286,7 +345,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
   const size_t o_sit = take(sizeof(StreamItem) * sitems.size());
   const size_t header_end = off;
   const size_t o_zero = off;
-  const size_t o_counter = take(sizeof(int));
+  const size_t o_counter = take(sizeof(int) * 8);
   for (auto& ip : plan) {
     ip.o_peak = take(sizeof(unsigned long long) * ip.k);
     ip.o_hist = take(sizeof(uint32_t) * ip.k * ip.J);
@@ -381,15 +440,22 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
   const ReduceItem* drit = reinterpret_cast<const ReduceItem*>(D + o_rit);
   const StreamItem* dsit = reinterpret_cast<const StreamItem*>(D + o_sit);
   int* dcounter = reinterpret_cast<int*>(D + o_counter);
-  int smem = 0;
-  for (auto& ip : plan) {
-    int rows = 0;
-    for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
-    smem = std::max(smem, rows * (ip.G / 2) * 4);
-  }
-  int ctas = (int)std::min<size_t>(vitems.size(), (size_t)nsm);
   VoteTimer vt(st);
-  launch_axis_vote(dvit, (int)vitems.size(), dinst, dcounter, ctas, smem, st);
+  for (size_t g = 0; g < groups.size(); ++g) {
+    const VoteGroup& vg = groups[g];
+    int nit = granges[g].second - granges[g].first;
+    if (nit == 0) continue;
+    const VoteItem* its = dvit + granges[g].first;
+    if (vg.C == 0) {
+      launch_axis_vote(its, nit, dinst, dcounter + g, std::min(nit, nsm), vg.smem, st);
+    } else if (vg.C == 1) {
+      launch_axis_vote_cluster(1, its, nit, dinst, dcounter + g, std::min(nit, nsm), vg.smem, st);
+    } else {
+      int ncl = std::max(1, active_clusters(ws->device, vg.C, vg.smem));
+      ncl = std::min(ncl, nit);
+      launch_axis_vote_cluster(vg.C, its, nit, dinst, dcounter + g, ncl * vg.C, vg.smem, st);
+    }
+  }
   vt.stop(st);
   launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
   for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
@@ -455,10 +521,13 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   std::lock_guard<std::mutex> lock(ws->mu);
   const int nsm = sm_count(ws->device);
   InstPlan ip{};
-  plan_bands(G, &ip.T, ip.row0);
-  int64_t s = std::max<int64_t>(1, nsm / ip.T);
-  s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
-  ip.S = (int)std::max<int64_t>(s, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
+  ip.G = G;
+  plan_vote(ip, n, true, ws->device, nsm);
+  if (ip.T <= 0) return SPROT_E_INVAL;
+  int rows = ip.G / std::max(ip.C, 1);
+  if (ip.C == 0)
+    for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+  const int smem = rows * (G / 2) * 4;
   std::vector<VoteItem> vit;
   for (int sl = 0; sl < ip.S; ++sl)
     for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
@@ -494,15 +563,21 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   std::memcpy(H + o_rit, rit.data(), sizeof(ReduceItem) * rit.size());
   if (cudaMemcpyAsync(D, H, hdr, cudaMemcpyHostToDevice, st) != cudaSuccess) return SPROT_E_CUDA;
   if (cudaMemsetAsync(D + o_zero, 0, zend - o_zero, st) != cudaSuccess) return SPROT_E_CUDA;
-  int rows = 0;
-  for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+  const VoteItem* dv = reinterpret_cast<VoteItem*>(D + o_vit);
+  const InstDev* di = reinterpret_cast<InstDev*>(D + o_inst);
+  int* dc = reinterpret_cast<int*>(D + o_zero);
+  const int nit = (int)vit.size();
   VoteTimer vt(st);
-  launch_axis_vote(reinterpret_cast<VoteItem*>(D + o_vit), (int)vit.size(),
-                   reinterpret_cast<InstDev*>(D + o_inst), reinterpret_cast<int*>(D + o_zero),
-                   (int)std::min<size_t>(vit.size(), (size_t)nsm), rows * (G / 2) * 4, st);
+  if (ip.C == 0)
+    launch_axis_vote(dv, nit, di, dc, std::min(nit, nsm), smem, st);
+  else if (ip.C == 1)
+    launch_axis_vote_cluster(1, dv, nit, di, dc, std::min(nit, nsm), smem, st);
+  else
+    launch_axis_vote_cluster(ip.C, dv, nit, di, dc,
+                             std::min(nit, std::max(1, active_clusters(ws->device, ip.C, smem))) * ip.C,
+                             smem, st);
   vt.stop(st);
-  launch_grid_reduce(reinterpret_cast<ReduceItem*>(D + o_rit), (int)rit.size(),
-                     reinterpret_cast<InstDev*>(D + o_inst), st);
+  launch_grid_reduce(reinterpret_cast<ReduceItem*>(D + o_rit), (int)rit.size(), di, st);
   if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
   // the host staging is reused by the next call: wait for the copy to have been consumed
   if (cudaStreamSynchronize(st) != cudaSuccess) return SPROT_E_CUDA;

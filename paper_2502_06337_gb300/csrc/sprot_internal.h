@@ -97,6 +97,12 @@ size_t problem_footprint(int64_t n, int G, int J, int k);
 // ---- launchers (kernels.cu) ------------------------------------------------------------
 void launch_axis_vote(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
                       int grid_ctas, int smem_bytes, cudaStream_t st);
+// Cluster axis vote (vote_cluster.cu): cluster size for a G x G accumulator (0 = too large,
+// use the banded kernel), co-resident clusters, and the launcher.
+int cluster_size_for(int G);
+int max_active_clusters(int C, int smem);
+void launch_axis_vote_cluster(int C, const VoteItem* items, int n_items, const InstDev* insts,
+                              int* counter, int n_ctas, int smem, cudaStream_t st);
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st);
 void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,

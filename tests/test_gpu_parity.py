@@ -191,3 +191,27 @@ def test_headline_scale(lib):
     parity.check_solve(prob.P, prob.Q, g, G, J, tau=tau)
     err = oracle.rotation_error(prob.rotations[0], g["rots"][0]["R"])
     assert err < math.radians(0.05)  # the paper reports about 0.01 degrees at this scale
+
+
+@pytest.mark.parametrize("G,n", [(1024, 60), (2048, 12)])
+def test_axis_vote_large_grids(lib, G, n):
+    """G = 1024 uses a 16-CTA cluster; G = 2048 does not fit one and uses row bands."""
+    prob = synth.make_problem(n, (0.5,), 0.01, seed=G + n)
+    av = oracle.axis_vote(prob.P, prob.Q, G)
+    parity.check_grid(_gpu_grid(prob.P, prob.Q, G), av, f"G={G}")
+
+
+def test_banded_kernel_matches_cluster_kernel(lib, monkeypatch):
+    """The row-band kernel (forced) and the cluster kernel give the same accumulator, and
+    both match the oracle."""
+    prob = synth.make_problem(700, (0.4,), 0.01, seed=77)
+    G = 512
+    a = _gpu_grid(prob.P, prob.Q, G)
+    monkeypatch.setenv("SPROT_VOTE_KERNEL", "banded")
+    b = _gpu_grid(prob.P, prob.Q, G)
+    monkeypatch.delenv("SPROT_VOTE_KERNEL")
+    av = oracle.axis_vote(prob.P, prob.Q, G)
+    parity.check_grid(a, av, "cluster")
+    parity.check_grid(b, av, "banded")
+    certain = av["lo"] == av["hi"]
+    assert np.array_equal(a[certain], b[certain])
