@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(256)
       lo += v & 0xffffu;
       hi += v >> 16;
     }
-    int row = (int)(w / W), c = (int)(w - (int64_t)row * W);
+    // word j of a row holds columns 2j (low half) and 2j + 1 (high half)
+    int row = (int)(w / W), c = 2 * (int)(w - (int64_t)row * W);
     D.grid[(int64_t)row * G + c] = lo;
-    D.grid[(int64_t)row * G + c + W] = hi;
+    D.grid[(int64_t)row * G + c + 1] = hi;
     unsigned long long k1 = peak_key(lo, (uint32_t)(row * G + c));
-    unsigned long long k2 = peak_key(hi, (uint32_t)(row * G + c + W));
+    unsigned long long k2 = peak_key(hi, (uint32_t)(row * G + c + 1));
     best = k1 > best ? k1 : best;
     best = k2 > best ? k2 : best;
   }
@@ -104,12 +105,12 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   unsigned long long best = 0;
-  // w indexes packed words; each covers cells (row, c) and (row, c + W).
+  // w indexes packed words; each covers cells (row, 2j) and (row, 2j + 1).
   for (int64_t w = I.w0 + threadIdx.x; w < I.w1; w += blockDim.x) {
-    int row = (int)(w / W), c0 = (int)(w - (int64_t)row * W);
+    int row = (int)(w / W), c0 = 2 * (int)(w - (int64_t)row * W);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      int col = c0 + h * W;
+      int col = c0 + h;
       uint32_t cnt = D.grid[(int64_t)row * G + col];
       if (!cnt) continue;
       unsigned long long key = peak_key(cnt, (uint32_t)(row * G + col));

@@ -98,7 +98,7 @@ int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, i
 // uniform density of the sphere), whose integral across a row is
 // (4 / a) atan(1 / a), a = sqrt(1 + v^2).
 void plan_bands(int G, int* n_bands, int32_t* row0) {
-  const int cap = kMaxSmemBytes / (G / 2 * 4);
+  const int cap = (kMaxSmemBytes - vote_table_bytes()) / (G / 2 * 4);
   std::vector<double> cum(G + 1, 0.0);
   for (int r = 0; r < G; ++r) {
     double v = -1.0 + (2.0 * r + 1.0) / G, a = std::sqrt(1.0 + v * v);
@@ -111,10 +111,12 @@ void plan_bands(int G, int* n_bands, int32_t* row0) {
     for (int b = 1; b < T; ++b) {
       double target = cum[G] * b / T;
       int r = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
-      e[b] = std::min(std::max(r, e[b - 1] + 1), G - (T - b));
+      int lo = std::max(e[b - 1] + 1, G - (T - b) * cap);  // the rest must still fit
+      int hi = std::min(e[b - 1] + cap, G - (T - b));
+      e[b] = std::min(std::max(r, lo), hi);
     }
     bool fits = true;
-    for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= cap;
+    for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= cap && e[b + 1] > e[b];
     if (fits) {
       *n_bands = T;
       for (int b = 0; b <= T; ++b) row0[b] = e[b];
@@ -130,7 +132,7 @@ struct InstPlan {
   int G, J, k, w, window;
   float tau;
   double cos_nms;
-  int T, S, C;  // bands (banded kernel), slices, cluster size (0 = banded kernel)
+  int T, S;  // row bands and circle slices of the axis vote
   int32_t row0[kMaxBands + 1];
   int chunk, n_items, item0;
   // arena offsets
@@ -207,52 +209,22 @@ int stream_chunk(int64_t n) {
   return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
 }
 
-// Co-resident clusters of the cluster vote kernel (cached per device and cluster size).
-int active_clusters(int dev, int C, int smem) {
-  static std::mutex mu;
-  static std::map<std::pair<int, int>, int> cache;
-  std::lock_guard<std::mutex> g(mu);
-  auto key = std::make_pair(dev, C);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  int v = max_active_clusters(C, smem);
-  cache[key] = v;
-  return v;
-}
-
-// Vote layout of one instance: the cluster kernel holds the whole accumulator in one CTA or
-// one cluster; G = 2048 does not fit a cluster and falls back to row bands.
-void plan_vote(InstPlan& ip, int64_t n, bool single, int dev, int nsm) {
-  ip.C = cluster_size_for(ip.G);
-  const char* force = std::getenv("SPROT_VOTE_KERNEL");  // "banded": measurement and tests
-  if (force && std::strcmp(force, "banded") == 0) ip.C = 0;
+// Vote layout of one instance: row bands that fit the shared tile, and circle slices (at most
+// 65535 circles each, so the 16-bit counters cannot overflow). A single problem is spread
+// over every SM; in a batch each instance gets slices of 32768 circles.
+void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm) {
+  plan_bands(ip.G, &ip.T, ip.row0);
   const int64_t s_min = (n + kMaxSliceCircles - 1) / kMaxSliceCircles;
-  int64_t s;
-  if (ip.C == 0) {
-    plan_bands(ip.G, &ip.T, ip.row0);
-    s = single ? std::max<int64_t>(1, nsm / std::max(ip.T, 1)) : (n + 32767) / 32768;
-  } else {
-    ip.T = 1;
-    ip.row0[0] = 0;
-    ip.row0[1] = ip.G;
-    if (single) {
-      int smem = (ip.G / ip.C) * (ip.G / 2) * 4;
-      s = ip.C == 1 ? nsm : std::max(1, active_clusters(dev, ip.C, smem));
-    } else {
-      s = (n + 32767) / 32768;
-    }
-  }
+  int64_t s = single ? std::max<int64_t>(1, nsm / std::max(ip.T, 1)) : (n + 32767) / 32768;
   s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
   ip.S = (int)std::max(s, s_min);
 }
 
-struct VoteGroup {
-  int C;  // 0 = banded
-  std::vector<VoteItem> items;
-  int smem = 0;
-};
-
-int group_index(int C) { return C == 0 ? 0 : 1 + __builtin_ctz((unsigned)C); }  // 0..5
+int tile_bytes(const InstPlan& ip) {
+  int rows = 0;
+  for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
+  return rows * (ip.G / 2) * 4;
+}
 
 }  // namespace
 
@@ -278,8 +250,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
 
   // ---- plan ---------------------------------------------------------------------------
   std::vector<InstPlan> plan(m);
-  std::vector<VoteGroup> groups(6);
   std::vector<VoteItem> vitems;
+  int vote_tile = 0;
   std::vector<ReduceItem> ritems;
   std::vector<StreamItem> sitems;
   int max_k = 1, max_J = 2;
@@ -294,19 +266,12 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
     ip.window = pb.prm.angle_window;
     ip.tau = (float)pb.prm.tau;
     ip.cos_nms = std::cos((double)pb.prm.nms_deg * 3.14159265358979323846 / 180.0);
-    plan_vote(ip, pb.n, m == 1, ws->device, nsm);
+    plan_vote(ip, pb.n, m == 1, nsm);
     if (ip.T <= 0) return SPROT_E_INVAL;
-    {
-      VoteGroup& vg = groups[group_index(ip.C)];
-      vg.C = ip.C;
-      int rows = 0;
-      for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
-      if (ip.C > 0) rows = ip.G / ip.C;
-      vg.smem = std::max(vg.smem, rows * (ip.G / 2) * 4);
-      for (int sl = 0; sl < ip.S; ++sl) {
-        int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
-        for (int b = 0; b < ip.T; ++b) vg.items.push_back(VoteItem{i, b, sl, 0, c0, c1});
-      }
+    vote_tile = std::max(vote_tile, tile_bytes(ip));
+    for (int sl = 0; sl < ip.S; ++sl) {
+      int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
+      for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
     }
     int64_t words = (int64_t)ip.G * (ip.G / 2);
     for (int64_t w0 = 0; w0 < words; w0 += 1024)
@@ -319,18 +284,12 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
     max_k = std::max(max_k, ip.k);
     max_J = std::max(max_J, ip.J);
   }
-  // Longest vote items first within each group (persistent CTAs finish together).
-  std::vector<std::pair<int, int>> granges;  // [begin, end) of each group in vitems
-  for (auto& vg : groups) {
-    std::stable_sort(vg.items.begin(), vg.items.end(), [&](const VoteItem& a, const VoteItem& b) {
-      double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
-      double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
-      return wa > wb;
-    });
-    int b0 = (int)vitems.size();
-    vitems.insert(vitems.end(), vg.items.begin(), vg.items.end());
-    granges.push_back({b0, (int)vitems.size()});
-  }
+  // Longest vote items first (the persistent CTAs then finish together).
+  std::stable_sort(vitems.begin(), vitems.end(), [&](const VoteItem& a, const VoteItem& b) {
+    double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
+    double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
+    return wa > wb;
+  });
 
   // ---- layout -------------------------------------------------------------------------
   size_t off = 0;
@@ -345,7 +304,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
   const size_t o_sit = take(sizeof(StreamItem) * sitems.size());
   const size_t header_end = off;
   const size_t o_zero = off;
-  const size_t o_counter = take(sizeof(int) * 8);
+  const size_t o_counter = take(sizeof(int));
   for (auto& ip : plan) {
     ip.o_peak = take(sizeof(unsigned long long) * ip.k);
     ip.o_hist = take(sizeof(uint32_t) * ip.k * ip.J);
@@ -441,21 +400,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
   const StreamItem* dsit = reinterpret_cast<const StreamItem*>(D + o_sit);
   int* dcounter = reinterpret_cast<int*>(D + o_counter);
   VoteTimer vt(st);
-  for (size_t g = 0; g < groups.size(); ++g) {
-    const VoteGroup& vg = groups[g];
-    int nit = granges[g].second - granges[g].first;
-    if (nit == 0) continue;
-    const VoteItem* its = dvit + granges[g].first;
-    if (vg.C == 0) {
-      launch_axis_vote(its, nit, dinst, dcounter + g, std::min(nit, nsm), vg.smem, st);
-    } else if (vg.C == 1) {
-      launch_axis_vote_cluster(1, its, nit, dinst, dcounter + g, std::min(nit, nsm), vg.smem, st);
-    } else {
-      int ncl = std::max(1, active_clusters(ws->device, vg.C, vg.smem));
-      ncl = std::min(ncl, nit);
-      launch_axis_vote_cluster(vg.C, its, nit, dinst, dcounter + g, ncl * vg.C, vg.smem, st);
-    }
-  }
+  launch_axis_vote_walk(dvit, (int)vitems.size(), dinst, dcounter,
+                        std::min((int)vitems.size(), nsm), vote_tile, st);
   vt.stop(st);
   launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
   for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
@@ -522,12 +468,9 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   const int nsm = sm_count(ws->device);
   InstPlan ip{};
   ip.G = G;
-  plan_vote(ip, n, true, ws->device, nsm);
+  plan_vote(ip, n, true, nsm);
   if (ip.T <= 0) return SPROT_E_INVAL;
-  int rows = ip.G / std::max(ip.C, 1);
-  if (ip.C == 0)
-    for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
-  const int smem = rows * (G / 2) * 4;
+  const int smem = tile_bytes(ip);
   std::vector<VoteItem> vit;
   for (int sl = 0; sl < ip.S; ++sl)
     for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
@@ -568,14 +511,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   int* dc = reinterpret_cast<int*>(D + o_zero);
   const int nit = (int)vit.size();
   VoteTimer vt(st);
-  if (ip.C == 0)
-    launch_axis_vote(dv, nit, di, dc, std::min(nit, nsm), smem, st);
-  else if (ip.C == 1)
-    launch_axis_vote_cluster(1, dv, nit, di, dc, std::min(nit, nsm), smem, st);
-  else
-    launch_axis_vote_cluster(ip.C, dv, nit, di, dc,
-                             std::min(nit, std::max(1, active_clusters(ws->device, ip.C, smem))) * ip.C,
-                             smem, st);
+  launch_axis_vote_walk(dv, nit, di, dc, std::min(nit, nsm), smem, st);
   vt.stop(st);
   launch_grid_reduce(reinterpret_cast<ReduceItem*>(D + o_rit), (int)rit.size(), di, st);
   if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;

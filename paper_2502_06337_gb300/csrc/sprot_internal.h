@@ -12,7 +12,6 @@ namespace sprot {
 
 constexpr int kMaxK = SPROT_MAX_K;
 constexpr int kMaxBands = 48;        // row bands of one accumulator (G = 2048 needs 37)
-constexpr int kVoteThreads = 1024;   // threads of the axis-vote CTA
 constexpr int kStreamThreads = 256;  // threads of the per-pair kernels
 constexpr int kStreamChunk = 8192;   // pairs per per-pair work item
 constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // tile; leaves room for static shared
@@ -42,7 +41,7 @@ struct InstDev {
   double cos_nms;                // cosine of the suppression radius between axis lines
   int32_t band_row0[kMaxBands + 1];
   // workspace
-  uint32_t* partial;             // [S][G][G/2] u16 pairs (col c and c + G/2 share a word)
+  uint32_t* partial;             // [S][G][G/2] u16 pairs (columns 2j and 2j+1 share a word)
   uint32_t* grid;                // [G][G]
   unsigned long long* peak_key;  // [k] packed (count, ~index) maxima
   uint32_t* hist;                // [k][J]
@@ -94,15 +93,12 @@ int solve(std::vector<Problem>& probs, cudaStream_t st);
 // Device bytes one problem occupies in a solve() workspace (inputs excluded).
 size_t problem_footprint(int64_t n, int G, int J, int k);
 
-// ---- launchers (kernels.cu) ------------------------------------------------------------
-void launch_axis_vote(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
-                      int grid_ctas, int smem_bytes, cudaStream_t st);
-// Cluster axis vote (vote_cluster.cu): cluster size for a G x G accumulator (0 = too large,
-// use the banded kernel), co-resident clusters, and the launcher.
-int cluster_size_for(int G);
-int max_active_clusters(int C, int smem);
-void launch_axis_vote_cluster(int C, const VoteItem* items, int n_items, const InstDev* insts,
-                              int* counter, int n_ctas, int smem, cudaStream_t st);
+// ---- launchers -------------------------------------------------------------------------
+// Axis vote (vote_walk.cu). tile_bytes: the largest band tile of the launch; the kernel adds
+// its per-warp circle tables (vote_table_bytes()) to the dynamic shared memory.
+int vote_table_bytes();
+void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
+                           int grid_ctas, int tile_bytes, cudaStream_t st);
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st);
 void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,

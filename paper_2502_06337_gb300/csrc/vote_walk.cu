@@ -1,0 +1,514 @@
+// Axis vote: the 2-D accumulator of Algorithm 1 (Sec. IV-A), rasterised exactly by walking
+// the projected circles cell by cell.
+//
+// Every correspondence i gives d = p_i - q_i; its admissible rotation axes form the great
+// circle r . d = 0 (Eqs. 5-8), whose stereographic image (Eqs. 11-13, D = 0) is the zero set of
+//     F(u, v) = 2 d1 u + 2 d2 v + d3 (u^2 + v^2 - 1).
+// After scaling d by a power of two and choosing its sign so that d3 >= 0, the curve is a
+// circle of centre (-d1, -d2)/d3 and radius |d|/d3 >= 1, or for d3 = 0 a line through the
+// origin. A cell is voted when the curve meets the closed cell.
+//
+// The circle is split at its four extreme points and four 45-degree points into eight
+// monotone pieces: four x-major pieces (|slope| <= 1), walked column by column, and four
+// y-major pieces, walked row by row (the same code with u and v exchanged). Walking a piece
+// along its major axis, the crossing moves by at most about one cell per step; whether it
+// passes the next lattice edge is the sign of F at the lattice corner (exact grid
+// coordinates, three roundings). The two cells of extreme points are voted directly.
+//
+// Work split. A CTA owns one row band of the accumulator as 16-bit counters in shared
+// memory (columns 2j and 2j+1 share a 32-bit word), incremented with red.shared.add.u32. A
+// warp loads 32 circles; in phase A each lane prepares its own circle for the band (piece
+// ranges culled to the band and the grid, extreme cells voted) and stores it in a per-warp
+// table. In phase B the pieces of all 32 circles are concatenated and each lane takes an
+// equal share of their major steps, so a lane restarts (one quadratic solve) only at piece
+// boundaries. One iteration of a lane votes one cell and then either crosses one lattice
+// edge of the minor axis -- when the piece is beyond that edge at the exit line, i.e. when
+// F at the lattice corner has the sign of "beyond" -- or advances one major step. F is
+// evaluated as g(x) + h(y) with g, h updated only when x or y changes, three roundings in
+// all. Decisions whose F is within a few float32 roundings of zero lie inside the band
+// where the closed-cell test may go either way; all others match the exact test.
+#include <stdint.h>
+
+#include "sprot_internal.h"
+
+namespace sprot {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float edgef(int k, float step) { return fmaf((float)k, step, -1.0f); }
+
+// Roots lo <= hi of c3 y^2 + 2 b y + kk = 0 (c3 >= 0, inv3 = 1/c3, +inf for c3 = 0), one from
+// |b| + sqrt(disc) and the other from the product of the roots. Returns false (roots NaN)
+// when the quadratic has no real root.
+__device__ __forceinline__ bool qroots(float c3, float inv3, float b, float kk, float& lo,
+                                       float& hi) {
+  const float disc = fmaf(-c3, kk, b * b);
+  const float t = fabsf(b) + sqrtf(disc);
+  const float far = t * inv3;
+  const float nr = t > 0.f ? kk * __frcp_rn(t) : 0.f;  // t = 0: b = 0, double root at 0
+  lo = b >= 0.f ? -far : nr;
+  hi = b >= 0.f ? -nr : far;
+  return disc >= 0.f;
+}
+
+// Cell of coordinate y clamped to [lo, hi] (NaN -> lo).
+__device__ __forceinline__ int cell_clamped(float y, float half, int lo, int hi) {
+  return __float2int_rd(fminf(fmaxf(fmaf(y, half, half), (float)lo), (float)hi));
+}
+
+struct Band {
+  uint32_t sbase;
+  int G, W, R0, R1;
+  float step, half, Gf;
+
+  __device__ __forceinline__ void vote(int r, int c) const {
+    const uint32_t word = (uint32_t)((r - R0) * W + (c >> 1));
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(sbase + 4u * word),
+                 "r"((c & 1) ? 0x10000u : 1u)
+                 : "memory");
+  }
+  __device__ __forceinline__ int cell(float y) const { return cell_clamped(y, half, -1, G); }
+  __device__ __forceinline__ int index(float y) const { return cell_clamped(y, half, -4, G + 4); }
+};
+
+// Piece p: 0-3 x-major (top-left, top-right, bottom-left, bottom-right), 4-7 y-major
+// (left-lower, left-upper, right-lower, right-upper). The branch is the upper root along the
+// minor axis for pieces 0, 1, 6, 7. kDirUp: pieces whose minor coordinate grows along the
+// major axis. For every piece, (direction) x (sign of dF/d(minor) on its branch) is +1 for
+// even p and -1 for odd p; even pieces walk toward the circle's centre, odd ones away.
+constexpr uint32_t kDirUp = 0x69u;
+
+struct Prepared {
+  float d1, d2, d3, inv3;
+  uint32_t piece[8];  // major range [lo, hi) packed lo | hi << 16
+  uint32_t jAB;       // y-major column windows: jA + 1 | jB << 16 (left <= jA, right >= jB)
+};
+
+__device__ __forceinline__ uint32_t pack(int lo, int hi) {
+  return hi > lo ? ((uint32_t)lo | ((uint32_t)hi << 16)) : 0u;
+}
+
+// Phase A (one lane, one circle): piece ranges for this band; extreme-point cells voted.
+__device__ void prepare(const Band& B, float d1, float d2, float d3, Prepared& S) {
+  const int G = B.G;
+  const float step = B.step;
+  const float V0 = edgef(B.R0, step), V1 = edgef(B.R1, step);
+  const float nd = sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
+  const float d1x2 = 2.f * d1, d2x2 = 2.f * d2;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) S.piece[p] = 0u;
+  S.d1 = d1;
+  S.d2 = d2;
+  if (d3 <= 1e-8f * nd) {
+    // a line through the origin (d3 = 0 up to a change of F below 2e-8 |d|)
+    S.d3 = 0.f;
+    S.inv3 = __int_as_float(0x7f800000);
+    const bool rise = d1 * d2 <= 0.f;
+    if (fabsf(d2) >= fabsf(d1)) {
+      const bool up = d2 >= 0.f;
+      const int p = up ? (rise ? 0 : 1) : (rise ? 3 : 2);
+      S.piece[p] = pack(0, G);
+      S.jAB = 0u | ((uint32_t)G << 16);
+    } else {
+      const bool up = d1 >= 0.f;
+      const int p = up ? (rise ? 6 : 7) : (rise ? 5 : 4);
+      S.piece[p] = pack(B.R0, B.R1);
+      S.jAB = (uint32_t)G | (0u << 16);  // both windows are the whole row
+    }
+    return;
+  }
+  S.d3 = d3;
+  const float inv3 = __frcp_rn(d3);
+  S.inv3 = inv3;
+  const float s = 0.70710678f;
+  // 45-degree points cx -/+ rho/sqrt(2), without cancellation
+  const float q1 = fmaf(d2, d2, d3 * d3) - d1 * d1;
+  const float uA = d1 >= 0.f ? -(d1 + s * nd) * inv3 : -0.5f * q1 / ((s * nd - d1) * d3);
+  const float uB = d1 <= 0.f ? (s * nd - d1) * inv3 : 0.5f * q1 / ((s * nd + d1) * d3);
+  const int jA = min(max(cell_clamped(uA, B.half, -2, G + 2), -1), G - 1);
+  const int jB = min(max(cell_clamped(uB, B.half, -2, G + 2), 0), G);
+  S.jAB = (uint32_t)(jA + 1) | ((uint32_t)jB << 16);
+  const int xj0 = max(jA + 1, 0), xj1 = min(jB - 1, G - 1);
+  const float cx = -d1 * inv3, cy = -d2 * inv3;
+  const int jc = B.index(cx), ic = B.index(cy);
+  float lo, hi, lo1, hi1;
+
+  // the column holding the top and bottom points
+  if (jc >= xj0 && jc <= xj1) {
+    float yb, yt;
+    qroots(d3, inv3, d2, -fmaf(d1, d1, d3 * d3) * inv3, yb, yt);
+    float x = edgef(jc, step);
+    qroots(d3, inv3, d2, fmaf(d3, fmaf(x, x, -1.f), d1x2 * x), lo, hi);
+    x = edgef(jc + 1, step);
+    qroots(d3, inv3, d2, fmaf(d3, fmaf(x, x, -1.f), d1x2 * x), lo1, hi1);
+    int a = max(min(B.cell(hi), B.cell(hi1)), B.R0), b = min(B.cell(yt), B.R1 - 1);
+    for (int r = a; r <= b; ++r) B.vote(r, jc);
+    a = max(B.cell(yb), B.R0);
+    b = min(max(B.cell(lo), B.cell(lo1)), B.R1 - 1);
+    for (int r = a; r <= b; ++r) B.vote(r, jc);
+  }
+
+  // x-major pieces, culled to the columns where they are inside the band [V0, V1]
+  {
+    float a0, b0, a1, b1;
+    const bool ok0 = qroots(d3, inv3, d1, fmaf(d3, fmaf(V0, V0, -1.f), d2x2 * V0), a0, b0);
+    const bool ok1 = qroots(d3, inv3, d1, fmaf(d3, fmaf(V1, V1, -1.f), d2x2 * V1), a1, b1);
+    const int L0 = xj0, L1 = min(jc, xj1 + 1), Rr0 = max(jc + 1, xj0), Rr1 = xj1 + 1;
+    // bounds: 'lo' restricts the first column, 'hi' the last; k = 0 none, 1 value, 2 empty
+    auto clip = [&](int a, int b, int klo, float ulo, int khi, float uhi) -> uint32_t {
+      if (klo == 2 || khi == 2) return 0u;
+      if (klo == 1) a = max(a, B.index(ulo) - 1);
+      if (khi == 1) b = min(b, B.index(uhi) + 2);
+      return pack(a, b);
+    };
+    // top-left: v >= V0 <=> u >= a0 ; v <= V1 <=> u <= a1
+    S.piece[0] = clip(L0, L1, V0 <= cy ? 0 : (ok0 ? 1 : 2), a0, V1 < cy ? 2 : (ok1 ? 1 : 0), a1);
+    // top-right: v >= V0 <=> u <= b0 ; v <= V1 <=> u >= b1
+    S.piece[1] = clip(Rr0, Rr1, V1 < cy ? 2 : (ok1 ? 1 : 0), b1, V0 <= cy ? 0 : (ok0 ? 1 : 2), b0);
+    // bottom-left: v <= V1 <=> u >= a1 ; v >= V0 <=> u <= a0
+    S.piece[2] = clip(L0, L1, V1 >= cy ? 0 : (ok1 ? 1 : 2), a1, V0 > cy ? 2 : (ok0 ? 1 : 0), a0);
+    // bottom-right: v >= V0 <=> u >= b0 ; v <= V1 <=> u <= b1
+    S.piece[3] = clip(Rr0, Rr1, V0 > cy ? 2 : (ok0 ? 1 : 0), b0, V1 >= cy ? 0 : (ok1 ? 1 : 2), b1);
+  }
+
+  // y-major pieces: rows of the chord at the split line, within the band and the grid
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? jA < 0 : jB > G - 1) continue;
+    float x = edgef(side == 0 ? jA + 1 : jB, step);
+    qroots(d3, inv3, d2, fmaf(d3, fmaf(x, x, -1.f), d1x2 * x), lo, hi);
+    const int y0 = max(B.index(lo) - 1, B.R0), y1 = min(B.index(hi) + 1, B.R1 - 1);
+    // rows where the arc is beyond u = -1 (left) or u = +1 (right) are outside the grid
+    x = side == 0 ? -1.f : 1.f;
+    const bool okg = qroots(d3, inv3, d2, fmaf(d3, fmaf(x, x, -1.f), d1x2 * x), lo, hi);
+    const int lower_end = okg ? min(ic, B.index(lo) + 2) : ic;
+    const int upper_beg = okg ? max(ic + 1, B.index(hi) - 1) : ic + 1;
+    S.piece[side == 0 ? 4 : 6] = pack(y0, min(lower_end, y1 + 1));
+    S.piece[side == 0 ? 5 : 7] = pack(max(upper_beg, y0), y1 + 1);
+    // the row holding the leftmost (rightmost) point
+    if (ic >= y0 && ic <= y1) {
+      float ul, ur;
+      qroots(d3, inv3, d1, -fmaf(d2, d2, d3 * d3) * inv3, ul, ur);
+      x = edgef(ic, step);
+      qroots(d3, inv3, d1, fmaf(d3, fmaf(x, x, -1.f), d2x2 * x), lo, hi);
+      x = edgef(ic + 1, step);
+      qroots(d3, inv3, d1, fmaf(d3, fmaf(x, x, -1.f), d2x2 * x), lo1, hi1);
+      if (side == 0) {
+        const int a = max(B.cell(ul), 0), b = min(max(B.cell(lo), B.cell(lo1)), jA);
+        for (int c = a; c <= b; ++c) B.vote(ic, c);
+      } else {
+        const int a = max(min(B.cell(hi), B.cell(hi1)), jB), b = min(B.cell(ur), G - 1);
+        for (int c = a; c <= b; ++c) B.vote(ic, c);
+      }
+    }
+  }
+}
+
+// p - q scaled by a power of two so that max |d_k| is in [1, 2), signed so d3 >= 0.
+__device__ __forceinline__ bool circle_of(const float* __restrict__ P, const float* __restrict__ Q,
+                                          int64_t i, float& d1, float& d2, float& d3) {
+  d1 = __ldg(P + 3 * i) - __ldg(Q + 3 * i);
+  d2 = __ldg(P + 3 * i + 1) - __ldg(Q + 3 * i + 1);
+  d3 = __ldg(P + 3 * i + 2) - __ldg(Q + 3 * i + 2);
+  const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
+  if (m == 0.f) return false;
+  const int e = ilogbf(m);
+  d1 = scalbnf(d1, -e);
+  d2 = scalbnf(d2, -e);
+  d3 = scalbnf(d3, -e);
+  if (d3 < 0.f) {
+    d1 = -d1;
+    d2 = -d2;
+    d3 = -d3;
+  }
+  return true;
+}
+
+// Per-warp circle table in shared memory, one column per lane (structure of arrays):
+// d1 d2 d3 inv3 jAB piece[0..7] offset, where offset is the circle's first segment in the
+// batch.
+constexpr int kRecWords = 14;
+constexpr int kTabWords = kRecWords * 32;
+constexpr int kWalkThreads = 512;  // 16 warps: room for the tables beside the tile
+constexpr int kWalkWarps = kWalkThreads / 32;
+
+__device__ __forceinline__ void store_rec(uint32_t* tab, int lane, const Prepared& S, int off) {
+  tab[0 * 32 + lane] = __float_as_uint(S.d1);
+  tab[1 * 32 + lane] = __float_as_uint(S.d2);
+  tab[2 * 32 + lane] = __float_as_uint(S.d3);
+  tab[3 * 32 + lane] = __float_as_uint(S.inv3);
+  tab[4 * 32 + lane] = S.jAB;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) tab[(5 + p) * 32 + lane] = S.piece[p];
+  tab[13 * 32 + lane] = (uint32_t)off;
+}
+
+// Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
+constexpr int kSeg = 32;
+
+__device__ __forceinline__ int segments_of(uint32_t pk) {
+  const int l = (int)(pk >> 16) - (int)(pk & 0xffffu);
+  return l > 0 ? (l + kSeg - 1) / kSeg : 0;
+}
+
+// Phase B (the whole warp, its batch of circles). The pieces of all circles are cut into
+// segments of at most kSeg major steps and dealt out in rounds of 32, one segment per lane,
+// so that every lane decodes its segment and solves its start quadratic at the same time.
+// One iteration advances one major step: it votes the cell, crosses the next minor edge if
+// the piece is beyond it at the exit line (voting that cell too), and steps on. A piece is
+// never steeper than about one cell per step; a rare second crossing takes a short loop.
+__device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
+                                           int lane) {
+  const int G = B.G;
+  const float step = B.step;
+  const int R0 = B.R0, W = B.W;
+  for (int base = 0; base < total_segs; base += 32) {
+    const int sid = base + lane;
+    int len = 0, c = 0, r = 0, dir = 1, wlo = 0, span = -1;
+    bool tr = false, flip = false;
+    float d3 = 0.f, dM2 = 0.f, dN2 = 0.f, xe = 0.f, gx = 0.f, yb = 0.f, h = 0.f, dys = 0.f;
+    if (sid < total_segs) {
+      // the circle: the largest k with first_segment[k] <= sid
+      int k = 0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1)
+        if ((int)tab[13 * 32 + k + s] <= sid) k += s;
+      const int loc = sid - (int)tab[13 * 32 + k];
+      // the piece and the segment within it
+      int p = 0, seg = 0, lo = 0, plen = 0, acc = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t pk = tab[(5 + q) * 32 + k];
+        const int nq = segments_of(pk);
+        if (nq > 0 && loc >= acc) {
+          p = q;
+          seg = loc - acc;
+          lo = (int)(pk & 0xffffu);
+          plen = (int)(pk >> 16) - lo;
+        }
+        acc += nq;
+      }
+      c = lo + seg * kSeg;
+      len = min(kSeg, plen - seg * kSeg);
+      const float d1 = __uint_as_float(tab[0 * 32 + k]), d2 = __uint_as_float(tab[1 * 32 + k]);
+      const float inv3 = __uint_as_float(tab[3 * 32 + k]);
+      d3 = __uint_as_float(tab[2 * 32 + k]);
+      const uint32_t jAB = tab[4 * 32 + k];
+      tr = p >= 4;
+      const bool up = p < 2 || p >= 6;
+      dir = ((kDirUp >> p) & 1u) ? 1 : -1;
+      flip = (p & 1) != 0;  // "beyond" is F < 0 for even pieces and F > 0 for odd ones
+      dM2 = 2.f * (tr ? d2 : d1);
+      const float dN = tr ? d1 : d2;
+      dN2 = 2.f * dN;
+      const int jA = (int)(jAB & 0xffffu) - 1, jB = (int)(jAB >> 16);
+      wlo = tr ? (p < 6 ? 0 : jB) : R0;
+      span = (tr ? (p < 6 ? jA : G - 1) : B.R1 - 1) - wlo;
+      // start: the crossing of this piece's branch with the major line c
+      xe = edgef(c, step);
+      float rlo, rhi;
+      if (qroots(d3, inv3, dN, fmaf(d3, fmaf(xe, xe, -1.f), dM2 * xe), rlo, rhi)) {
+        r = B.cell(up ? rhi : rlo);
+      } else if (!flip) {
+        // The start line misses the circle (a margin row of a y-major piece): even pieces
+        // walk toward the centre, so start at the centre's column, which lies inside every
+        // chord of the circle and outside the piece's column window. If the next line meets
+        // the circle, the walk sweeps from there to the branch, voting exactly the cells of
+        // the cap in this row; if it does not, nothing moves.
+        r = B.cell(-dN * inv3);
+      } else {
+        len = 0;  // odd pieces walk away from the centre: the rest lies beyond the circle
+      }
+      dys = dir > 0 ? step : -step;
+      xe += step;  // exit line of column c
+      gx = xe * fmaf(d3, xe, dM2);
+      yb = edgef(r + (dir > 0 ? 1 : 0), step);  // next minor edge in the walking direction
+      h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
+    }
+    const int rlim = dir > 0 ? G : -1;  // crossing stops beyond the grid edge
+    const int rounds = __reduce_max_sync(kFull, (unsigned)len);
+    for (int i = 0; i < rounds; ++i) {
+      const bool act = i < len;
+      if (act && (unsigned)(r - wlo) <= (unsigned)span) {
+        const int row = tr ? c : r, col = tr ? r : c;
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
+                     "r"((col & 1) ? 0x10000u : 1u)
+                     : "memory");
+      }
+      float F = gx + h;
+      bool mv = act && (flip ? F > 0.f : F < 0.f) && r != rlim;
+      if (mv) {
+        r += dir;
+        yb += dys;
+        h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
+        if ((unsigned)(r - wlo) <= (unsigned)span) {
+          const int row = tr ? c : r, col = tr ? r : c;
+          asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
+                       "r"((col & 1) ? 0x10000u : 1u)
+                       : "memory");
+        }
+        F = gx + h;
+        // a second crossing in the same step is rare (slopes above one cell per step)
+        while ((flip ? F > 0.f : F < 0.f) && r != rlim) {
+          r += dir;
+          yb += dys;
+          h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
+          if ((unsigned)(r - wlo) <= (unsigned)span) {
+            const int row = tr ? c : r, col = tr ? r : c;
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
+                         "r"((col & 1) ? 0x10000u : 1u)
+                         : "memory");
+          }
+          F = gx + h;
+        }
+      }
+      c += 1;
+      xe += step;
+      gx = xe * fmaf(d3, xe, dM2);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWalkThreads, 1)
+    k_axis_vote_walk(const VoteItem* __restrict__ items, int n_items,
+                     const InstDev* __restrict__ insts, int* __restrict__ counter, int tile_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* tile = smem;
+  __shared__ int s_item, s_next;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* tab = smem + tile_words + warp * kTabWords;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(counter, 1);
+      s_next = 0;
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const VoteItem I = items[it];
+    const InstDev& D = insts[I.inst];
+    Band B;
+    B.G = D.G;
+    B.W = D.G >> 1;
+    B.R0 = D.band_row0[I.band];
+    B.R1 = D.band_row0[I.band + 1];
+    B.Gf = (float)D.G;
+    B.step = 2.0f / B.Gf;
+    B.half = 0.5f * B.Gf;
+    B.sbase = (uint32_t)__cvta_generic_to_shared(tile);
+    const int words = (B.R1 - B.R0) * B.W;
+    uint4* t4 = reinterpret_cast<uint4*>(tile);
+    for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+
+    const float* __restrict__ P = D.P;
+    const float* __restrict__ Q = D.Q;
+    const int64_t count = I.c1 - I.c0;
+    for (;;) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&s_next, 32);
+      base = __shfl_sync(kFull, base, 0);
+      if (base >= count) break;
+      float e1 = 0.f, e2 = 0.f, e3 = 0.f;
+      bool live = false;
+      if (base + lane < count) live = circle_of(P, Q, I.c0 + base + lane, e1, e2, e3);
+      // phase A: this lane's circle
+      Prepared S;
+      int steps = 0;  // segments of this circle
+      if (live) {
+        prepare(B, e1, e2, e3, S);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) steps += segments_of(S.piece[p]);
+      }
+      int incl = steps;
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, s);
+        if (lane >= s) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      if (live) {
+        store_rec(tab, lane, S, incl - steps);
+      } else {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) tab[(5 + p) * 32 + lane] = 0u;
+        tab[13 * 32 + lane] = (uint32_t)(incl - steps);
+      }
+      __syncwarp();
+      // phase B: the whole batch
+      if (total > 0) walk_batch(B, tab, total, lane);
+      __syncwarp();
+    }
+    __syncthreads();
+
+    // the band -> this slice's partial
+    uint4* out = reinterpret_cast<uint4*>(D.partial + ((int64_t)I.slice * D.G + B.R0) * B.W);
+    for (int g = threadIdx.x; g < (words >> 2); g += blockDim.x) out[g] = t4[g];
+    __syncthreads();
+  }
+}
+
+// Shared-atomic throughput probe: conflict-free red.shared.add.u32, one per thread per
+// round, on every SM.
+__global__ void __launch_bounds__(1024) k_probe_atomics(int iters, uint32_t* sink) {
+  __shared__ uint32_t buf[1024];
+  buf[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(buf + threadIdx.x);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(1u) : "memory");
+  }
+  __syncthreads();
+  if (buf[threadIdx.x] != (uint32_t)iters * 16u) atomicAdd(sink, 1u);
+}
+
+}  // namespace
+
+int vote_table_bytes() { return kWalkWarps * kTabWords * 4; }
+
+void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
+                           int grid_ctas, int tile_bytes, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_axis_vote_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kMaxSmemBytes);
+    attr = true;
+  }
+  k_axis_vote_walk<<<grid_ctas, kWalkThreads, tile_bytes + vote_table_bytes(), st>>>(
+      items, n_items, insts, counter, tile_bytes / 4);
+  launches_add(1);
+}
+
+double probe_smem_atomics(int iters, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t* sink = nullptr;
+  if (cudaMalloc(&sink, 4) != cudaSuccess) return -1.0;
+  cudaMemsetAsync(sink, 0, 4, st);
+  const int ctas = sms * 2;
+  k_probe_atomics<<<ctas, 1024, 0, st>>>(4, sink);  // warm-up
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  k_probe_atomics<<<ctas, 1024, 0, st>>>(iters, sink);
+  cudaEventRecord(b, st);
+  launches_add(2);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  uint32_t bad = 0;
+  cudaMemcpy(&bad, sink, 4, cudaMemcpyDeviceToHost);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (bad != 0 || ms <= 0.f) return -1.0;
+  return (double)ctas * 1024.0 * iters * 16.0 / (ms * 1e-3);
+}
+
+}  // namespace sprot

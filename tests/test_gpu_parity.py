@@ -195,23 +195,18 @@ def test_headline_scale(lib):
 
 @pytest.mark.parametrize("G,n", [(1024, 60), (2048, 12)])
 def test_axis_vote_large_grids(lib, G, n):
-    """G = 1024 uses a 16-CTA cluster; G = 2048 does not fit one and uses row bands."""
+    """G = 1024 and 2048 need 11 and 42 row bands of the shared-memory tile."""
     prob = synth.make_problem(n, (0.5,), 0.01, seed=G + n)
     av = oracle.axis_vote(prob.P, prob.Q, G)
     parity.check_grid(_gpu_grid(prob.P, prob.Q, G), av, f"G={G}")
 
 
-def test_banded_kernel_matches_cluster_kernel(lib, monkeypatch):
-    """The row-band kernel (forced) and the cluster kernel give the same accumulator, and
-    both match the oracle."""
-    prob = synth.make_problem(700, (0.4,), 0.01, seed=77)
-    G = 512
-    a = _gpu_grid(prob.P, prob.Q, G)
-    monkeypatch.setenv("SPROT_VOTE_KERNEL", "banded")
-    b = _gpu_grid(prob.P, prob.Q, G)
-    monkeypatch.delenv("SPROT_VOTE_KERNEL")
-    av = oracle.axis_vote(prob.P, prob.Q, G)
-    parity.check_grid(a, av, "cluster")
-    parity.check_grid(b, av, "banded")
-    certain = av["lo"] == av["hi"]
-    assert np.array_equal(a[certain], b[certain])
+@pytest.mark.parametrize("G", [16, 32, 512])
+def test_axis_vote_small_radius_circles(lib, G):
+    """Circles of radius close to 1 (|d3| dominant): at coarse grids the rows next to their
+    45-degree points reach past the top or bottom of the circle."""
+    rng = np.random.default_rng(11 + G)
+    D = rng.standard_normal((400, 3)).astype(np.float32)
+    D[:, 2] = np.sign(D[:, 2]) * (2 + 3 * np.abs(D[:, 2]))
+    P, Q = D, np.zeros_like(D)
+    parity.check_grid(_gpu_grid(P, Q, G), oracle.axis_vote(P, Q, G), f"small radius G={G}")
