@@ -462,14 +462,14 @@ __device__ void jacobi4_top(double A[4][4], double v[4]) {
   double V[4][4];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 64; ++sweep) {
+  for (int sweep = 0; sweep < 24; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int i = 0; i < 4; ++i)
       for (int j = 0; j < 4; ++j) {
         tot += A[i][j] * A[i][j];
         if (i != j) off += A[i][j] * A[i][j];
       }
-    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (off <= 1e-28 * tot || off == 0.0) break;
     for (int p = 0; p < 3; ++p)
       for (int q = p + 1; q < 4; ++q) {
         double apq = A[p][q];
@@ -528,6 +528,43 @@ __device__ void horn_rotation(const double* M, double* R) {
   R[8] = w * w - x * x - y * y + z * z;
 }
 
+// Rotation maximising tr(R^T M) when det M > 0: the orthogonal polar factor of M (M = U S V^T
+// gives U V^T, which is Kabsch's solution with no reflection to correct). Scaled Newton
+// iteration X <- (g X + X^{-T} / g) / 2 with g = sqrt(|X^{-1}|_F / |X|_F) (Higham), converging
+// quadratically; X^{-T} is the cofactor matrix over the determinant. Returns false (R not
+// written) when M is singular or reflecting to working precision.
+__device__ bool polar_rotation(const double* M, double* R) {
+  double X[9];
+  double n2 = 0.0;
+  for (int t = 0; t < 9; ++t) n2 += M[t] * M[t];
+  if (!(n2 > 0.0)) return false;
+  const double inv = 1.0 / sqrt(n2);
+  for (int t = 0; t < 9; ++t) X[t] = M[t] * inv;
+  for (int it = 0; it < 40; ++it) {
+    const double C[9] = {X[4] * X[8] - X[5] * X[7], X[5] * X[6] - X[3] * X[8], X[3] * X[7] - X[4] * X[6],
+                         X[2] * X[7] - X[1] * X[8], X[0] * X[8] - X[2] * X[6], X[1] * X[6] - X[0] * X[7],
+                         X[1] * X[5] - X[2] * X[4], X[2] * X[3] - X[0] * X[5], X[0] * X[4] - X[1] * X[3]};
+    const double det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    double xn = 0.0, cn = 0.0;
+    for (int t = 0; t < 9; ++t) {
+      xn += X[t] * X[t];
+      cn += C[t] * C[t];
+    }
+    if (it == 0 && !(det > 1e-9 * xn * sqrt(xn))) return false;  // singular or reflecting
+    const double g = sqrt(sqrt(cn / xn) / fabs(det));
+    const double a = 0.5 * g, b = 0.5 / (g * det);
+    double diff = 0.0;
+    for (int t = 0; t < 9; ++t) {
+      const double y = a * X[t] + b * C[t];
+      diff += (y - X[t]) * (y - X[t]);
+      X[t] = y;
+    }
+    if (diff < 1e-30) break;
+  }
+  for (int t = 0; t < 9; ++t) R[t] = X[t];
+  return true;
+}
+
 // phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One warp per
 // (instance, rotation); the item partials are summed in a fixed order.
 __global__ void k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
@@ -548,8 +585,8 @@ __global__ void k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase
   if (cnt == 0) {
     const double* fb = phase == 0 ? R.R_vote : R.R_init;
     for (int t = 0; t < 9; ++t) out[t] = fb[t];
-  } else {
-    horn_rotation(s, out);
+  } else if (!polar_rotation(s, out)) {
+    horn_rotation(s, out);  // reflecting or rank-deficient sums
   }
   if (phase == 0) {
     for (int t = 0; t < 9; ++t) {
