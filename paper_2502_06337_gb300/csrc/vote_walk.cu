@@ -253,120 +253,162 @@ __device__ __forceinline__ int segments_of(uint32_t pk) {
   return l > 0 ? (l + kSeg - 1) / kSeg : 0;
 }
 
-// Phase B (the whole warp, its batch of circles). The pieces of all circles are cut into
-// segments of at most kSeg major steps and dealt out in rounds of 32, one segment per lane,
-// so that every lane decodes its segment and solves its start quadratic at the same time.
-// One iteration advances one major step: it votes the cell, crosses the next minor edge if
-// the piece is beyond it at the exit line (voting that cell too), and steps on. A piece is
-// never steeper than about one cell per step; a rare second crossing takes a short loop.
-__device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
-                                           int lane) {
+// One walker: a segment of one piece, advanced one major step per iteration. The cell is
+// tracked as a half-word index into the band tile (two u16 counters per word) and as its
+// minor coordinate relative to the piece's window; the crossing test is F < 0 for every
+// piece (the coefficients of odd pieces are negated, which negates F exactly).
+struct Walker {
+  int len, hidx, rel, span, rlim, dmaj, dmin, dir;
+  float d3, dM2, dN2, xe, gx, yb, h, dys;
+};
+
+__device__ __forceinline__ void vote_if(const Band& B, bool cond, int hidx) {
+  const uint32_t addr = B.sbase + ((uint32_t)(hidx >> 1) << 2);
+  const uint32_t inc = 1u << ((hidx & 1) << 4);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
+      "r"(inc), "r"((int)cond)
+      : "memory");
+}
+
+// Decodes segment sid of the batch and places the walker on its first cell (len = 0 if none).
+__device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab, int total_segs,
+                                             int sid, Walker& w) {
   const int G = B.G;
   const float step = B.step;
-  const int R0 = B.R0, W = B.W;
-  for (int base = 0; base < total_segs; base += 32) {
-    const int sid = base + lane;
-    int len = 0, c = 0, r = 0, dir = 1, wlo = 0, span = -1;
-    bool tr = false, flip = false;
-    float d3 = 0.f, dM2 = 0.f, dN2 = 0.f, xe = 0.f, gx = 0.f, yb = 0.f, h = 0.f, dys = 0.f;
-    if (sid < total_segs) {
-      // the circle: the largest k with first_segment[k] <= sid
-      int k = 0;
+  w.len = 0;
+  w.hidx = 0;
+  w.rel = -1;
+  w.span = -1;
+  w.rlim = 0;
+  w.dmaj = w.dmin = 0;
+  w.dir = 1;
+  w.d3 = w.dM2 = w.dN2 = w.xe = w.gx = w.yb = w.h = w.dys = 0.f;
+  if (sid >= total_segs) return;
+  // the circle: the largest k with first_segment[k] <= sid
+  int k = 0;
 #pragma unroll
-      for (int s = 16; s > 0; s >>= 1)
-        if ((int)tab[13 * 32 + k + s] <= sid) k += s;
-      const int loc = sid - (int)tab[13 * 32 + k];
-      // the piece and the segment within it
-      int p = 0, seg = 0, lo = 0, plen = 0, acc = 0;
+  for (int s = 16; s > 0; s >>= 1)
+    if ((int)tab[13 * 32 + k + s] <= sid) k += s;
+  const int loc = sid - (int)tab[13 * 32 + k];
+  // the piece and the segment within it
+  int p = 0, seg = 0, lo = 0, plen = 0, acc = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t pk = tab[(5 + q) * 32 + k];
-        const int nq = segments_of(pk);
-        if (nq > 0 && loc >= acc) {
-          p = q;
-          seg = loc - acc;
-          lo = (int)(pk & 0xffffu);
-          plen = (int)(pk >> 16) - lo;
-        }
-        acc += nq;
-      }
-      c = lo + seg * kSeg;
-      len = min(kSeg, plen - seg * kSeg);
-      const float d1 = __uint_as_float(tab[0 * 32 + k]), d2 = __uint_as_float(tab[1 * 32 + k]);
-      const float inv3 = __uint_as_float(tab[3 * 32 + k]);
-      d3 = __uint_as_float(tab[2 * 32 + k]);
-      const uint32_t jAB = tab[4 * 32 + k];
-      tr = p >= 4;
-      const bool up = p < 2 || p >= 6;
-      dir = ((kDirUp >> p) & 1u) ? 1 : -1;
-      flip = (p & 1) != 0;  // "beyond" is F < 0 for even pieces and F > 0 for odd ones
-      dM2 = 2.f * (tr ? d2 : d1);
-      const float dN = tr ? d1 : d2;
-      dN2 = 2.f * dN;
-      const int jA = (int)(jAB & 0xffffu) - 1, jB = (int)(jAB >> 16);
-      wlo = tr ? (p < 6 ? 0 : jB) : R0;
-      span = (tr ? (p < 6 ? jA : G - 1) : B.R1 - 1) - wlo;
-      // start: the crossing of this piece's branch with the major line c
-      xe = edgef(c, step);
-      float rlo, rhi;
-      if (qroots(d3, inv3, dN, fmaf(d3, fmaf(xe, xe, -1.f), dM2 * xe), rlo, rhi)) {
-        r = B.cell(up ? rhi : rlo);
-      } else if (!flip) {
-        // The start line misses the circle (a margin row of a y-major piece): even pieces
-        // walk toward the centre, so start at the centre's column, which lies inside every
-        // chord of the circle and outside the piece's column window. If the next line meets
-        // the circle, the walk sweeps from there to the branch, voting exactly the cells of
-        // the cap in this row; if it does not, nothing moves.
-        r = B.cell(-dN * inv3);
-      } else {
-        len = 0;  // odd pieces walk away from the centre: the rest lies beyond the circle
-      }
-      dys = dir > 0 ? step : -step;
-      xe += step;  // exit line of column c
-      gx = xe * fmaf(d3, xe, dM2);
-      yb = edgef(r + (dir > 0 ? 1 : 0), step);  // next minor edge in the walking direction
-      h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t pk = tab[(5 + q) * 32 + k];
+    const int nq = segments_of(pk);
+    if (nq > 0 && loc >= acc) {
+      p = q;
+      seg = loc - acc;
+      lo = (int)(pk & 0xffffu);
+      plen = (int)(pk >> 16) - lo;
     }
-    const int rlim = dir > 0 ? G : -1;  // crossing stops beyond the grid edge
-    const int rounds = __reduce_max_sync(kFull, (unsigned)len);
+    acc += nq;
+  }
+  const int c = lo + seg * kSeg;
+  int len = min(kSeg, plen - seg * kSeg);
+  const float d1 = __uint_as_float(tab[0 * 32 + k]), d2 = __uint_as_float(tab[1 * 32 + k]);
+  const float inv3 = __uint_as_float(tab[3 * 32 + k]);
+  const float d3 = __uint_as_float(tab[2 * 32 + k]);
+  const uint32_t jAB = tab[4 * 32 + k];
+  const bool tr = p >= 4;
+  const bool up = p < 2 || p >= 6;
+  const int dir = ((kDirUp >> p) & 1u) ? 1 : -1;
+  const bool flip = (p & 1) != 0;  // "beyond" is F < 0 for even pieces and F > 0 for odd ones
+  const float dM2 = 2.f * (tr ? d2 : d1);
+  const float dN = tr ? d1 : d2;
+  const float dN2 = 2.f * dN;
+  const int jA = (int)(jAB & 0xffffu) - 1, jB = (int)(jAB >> 16);
+  const int wlo = tr ? (p < 6 ? 0 : jB) : B.R0;
+  w.span = (tr ? (p < 6 ? jA : G - 1) : B.R1 - 1) - wlo;
+  // start: the crossing of this piece's branch with the major line c
+  const float x = edgef(c, step);
+  float rlo, rhi;
+  int r;
+  if (qroots(d3, inv3, dN, fmaf(d3, fmaf(x, x, -1.f), dM2 * x), rlo, rhi)) {
+    r = B.cell(up ? rhi : rlo);
+  } else if (!flip) {
+    // The start line misses the circle (a margin row of a y-major piece): even pieces walk
+    // toward the centre, so start at the centre's column, which lies inside every chord of
+    // the circle and outside the piece's column window. If the next line meets the circle,
+    // the walk sweeps from there to the branch, voting exactly the cells of the cap in this
+    // row; if it does not, nothing moves.
+    r = B.cell(-dN * inv3);
+  } else {
+    r = 0;
+    len = 0;  // odd pieces walk away from the centre: the rest lies beyond the circle
+  }
+  w.len = len;
+  w.dir = dir;
+  w.rel = r - wlo;
+  w.rlim = (dir > 0 ? G : -1) - wlo;  // crossing stops beyond the grid edge
+  const int W2 = 2 * B.W;              // half-words per tile row
+  const int row = tr ? c : r, col = tr ? r : c;
+  w.hidx = (row - B.R0) * W2 + col;
+  w.dmaj = tr ? W2 : 1;
+  w.dmin = tr ? dir : dir * W2;
+  const float sg = flip ? -1.f : 1.f;
+  w.d3 = sg * d3;
+  w.dM2 = sg * dM2;
+  w.dN2 = sg * dN2;
+  w.dys = dir > 0 ? step : -step;
+  w.xe = x + step;  // exit line of column c
+  w.gx = w.xe * fmaf(w.d3, w.xe, w.dM2);
+  w.yb = edgef(r + (dir > 0 ? 1 : 0), step);  // next minor edge in the walking direction
+  w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
+}
+
+// One major step of a walker, straight-line: vote the cell, cross the next minor edge if the
+// piece is beyond it at the exit line (voting that cell), step on. Returns whether the piece
+// is still beyond the following edge (a second crossing in the same step, which is rare).
+__device__ __forceinline__ bool step_walker(const Band& B, Walker& w, bool act) {
+  vote_if(B, act && (unsigned)w.rel <= (unsigned)w.span, w.hidx);
+  const bool mv = act && (w.gx + w.h < 0.f) && w.rel != w.rlim;
+  w.rel += mv ? w.dir : 0;
+  w.hidx += mv ? w.dmin : 0;
+  w.yb += mv ? w.dys : 0.f;
+  w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
+  vote_if(B, mv && (unsigned)w.rel <= (unsigned)w.span, w.hidx);
+  return mv && (w.gx + w.h < 0.f) && w.rel != w.rlim;
+}
+
+// Remaining crossings of a step (slopes above one cell per step; rare).
+__device__ __forceinline__ void more_crossings(const Band& B, Walker& w) {
+  while (w.gx + w.h < 0.f && w.rel != w.rlim) {
+    w.rel += w.dir;
+    w.hidx += w.dmin;
+    w.yb += w.dys;
+    w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
+    vote_if(B, (unsigned)w.rel <= (unsigned)w.span, w.hidx);
+  }
+}
+
+__device__ __forceinline__ void advance(Walker& w, float step) {
+  w.hidx += w.dmaj;
+  w.xe += step;
+  w.gx = w.xe * fmaf(w.d3, w.xe, w.dM2);
+}
+
+// Phase B (the whole warp, its batch of circles). The pieces of all circles are cut into
+// segments of at most kSeg major steps and dealt out in rounds, two segments per lane, so
+// that every lane decodes its segments and solves their start quadratics at the same time
+// and walks two independent segments in lock step.
+__device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
+                                           int lane) {
+  for (int base = 0; base < total_segs; base += 64) {
+    Walker a, b;
+    start_walker(B, tab, total_segs, base + lane, a);
+    start_walker(B, tab, total_segs, base + 32 + lane, b);
+    const int rounds = __reduce_max_sync(kFull, (unsigned)max(a.len, b.len));
     for (int i = 0; i < rounds; ++i) {
-      const bool act = i < len;
-      if (act && (unsigned)(r - wlo) <= (unsigned)span) {
-        const int row = tr ? c : r, col = tr ? r : c;
-        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
-                     "r"((col & 1) ? 0x10000u : 1u)
-                     : "memory");
+      const bool more_a = step_walker(B, a, i < a.len);
+      const bool more_b = step_walker(B, b, i < b.len);
+      if (__any_sync(kFull, more_a || more_b)) {
+        if (more_a) more_crossings(B, a);
+        if (more_b) more_crossings(B, b);
       }
-      float F = gx + h;
-      bool mv = act && (flip ? F > 0.f : F < 0.f) && r != rlim;
-      if (mv) {
-        r += dir;
-        yb += dys;
-        h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
-        if ((unsigned)(r - wlo) <= (unsigned)span) {
-          const int row = tr ? c : r, col = tr ? r : c;
-          asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
-                       "r"((col & 1) ? 0x10000u : 1u)
-                       : "memory");
-        }
-        F = gx + h;
-        // a second crossing in the same step is rare (slopes above one cell per step)
-        while ((flip ? F > 0.f : F < 0.f) && r != rlim) {
-          r += dir;
-          yb += dys;
-          h = fmaf(yb, fmaf(d3, yb, dN2), -d3);
-          if ((unsigned)(r - wlo) <= (unsigned)span) {
-            const int row = tr ? c : r, col = tr ? r : c;
-            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(B.sbase + 4u * (uint32_t)((row - R0) * W + (col >> 1))),
-                         "r"((col & 1) ? 0x10000u : 1u)
-                         : "memory");
-          }
-          F = gx + h;
-        }
-      }
-      c += 1;
-      xe += step;
-      gx = xe * fmaf(d3, xe, dM2);
+      advance(a, B.step);
+      advance(b, B.step);
     }
   }
 }
