@@ -246,7 +246,8 @@ __device__ __forceinline__ void store_rec(uint32_t* tab, int lane, const Prepare
 }
 
 // Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
-constexpr int kSeg = 32;
+constexpr int kSeg = 16;
+constexpr int kWalkers = 3;
 
 __device__ __forceinline__ int segments_of(uint32_t pk) {
   const int l = (int)(pk >> 16) - (int)(pk & 0xffffu);
@@ -254,19 +255,22 @@ __device__ __forceinline__ int segments_of(uint32_t pk) {
 }
 
 // One walker: a segment of one piece, advanced one major step per iteration. The cell is
-// tracked as a half-word index into the band tile (two u16 counters per word) and as its
-// minor coordinate relative to the piece's window; the crossing test is F < 0 for every
-// piece (the coefficients of odd pieces are negated, which negates F exactly).
+// tracked as a half-word index hb into the tile (two u16 counters per word, offset so that
+// the word's shared address is (hb << 1) & ~3) with the increment inc = 1 or 0x10000 for
+// its half, and as its minor coordinate rel relative to the piece's window. The crossing
+// test is gx < -h (F < 0) for every piece: the coefficients of odd pieces are negated, which
+// negates F exactly, and without flush to zero the sign of a rounded sum is the sign of the
+// exact one.
 struct Walker {
-  int len, hidx, rel, span, rlim, dmaj, dmin, dir;
+  int len, hb, rel, span, rlim, dmaj, dmin, dir;
+  uint32_t inc, fmaj;  // fmaj: the flip of inc on a major step (the minor flip is its complement)
   float d3, dM2, dN2, xe, gx, yb, h, dys;
 };
 
-__device__ __forceinline__ void vote_if(const Band& B, bool cond, int hidx) {
-  const uint32_t addr = B.sbase + ((uint32_t)(hidx >> 1) << 2);
-  const uint32_t inc = 1u << ((hidx & 1) << 4);
+__device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr),
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(
+          (uint32_t)(hb << 1) & ~3u),
       "r"(inc), "r"((int)cond)
       : "memory");
 }
@@ -277,12 +281,14 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   const int G = B.G;
   const float step = B.step;
   w.len = 0;
-  w.hidx = 0;
+  w.hb = 0;
   w.rel = -1;
   w.span = -1;
   w.rlim = 0;
   w.dmaj = w.dmin = 0;
   w.dir = 1;
+  w.inc = 1u;
+  w.fmaj = 0u;
   w.d3 = w.dM2 = w.dN2 = w.xe = w.gx = w.yb = w.h = w.dys = 0.f;
   if (sid >= total_segs) return;
   // the circle: the largest k with first_segment[k] <= sid
@@ -341,10 +347,12 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.len = len;
   w.dir = dir;
   w.rel = r - wlo;
-  w.rlim = (dir > 0 ? G : -1) - wlo;  // crossing stops beyond the grid edge
+  w.rlim = (dir > 0 ? G : -1) - wlo;  // the rare-crossing loop stops at the grid edge
   const int W2 = 2 * B.W;              // half-words per tile row
   const int row = tr ? c : r, col = tr ? r : c;
-  w.hidx = (row - B.R0) * W2 + col;
+  w.hb = (row - B.R0) * W2 + col + (int)(B.sbase >> 1);
+  w.inc = (col & 1) ? 0x10000u : 1u;
+  w.fmaj = tr ? 0u : 0x10001u;
   w.dmaj = tr ? W2 : 1;
   w.dmin = tr ? dir : dir * W2;
   const float sg = flip ? -1.f : 1.f;
@@ -361,54 +369,69 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
 // One major step of a walker, straight-line: vote the cell, cross the next minor edge if the
 // piece is beyond it at the exit line (voting that cell), step on. Returns whether the piece
 // is still beyond the following edge (a second crossing in the same step, which is rare).
-__device__ __forceinline__ bool step_walker(const Band& B, Walker& w, bool act) {
-  vote_if(B, act && (unsigned)w.rel <= (unsigned)w.span, w.hidx);
-  const bool mv = act && (w.gx + w.h < 0.f) && w.rel != w.rlim;
+// A walker that leaves the grid never returns (each piece is monotone along its minor axis)
+// and its votes are masked by the window test, so the common step does not stop at the edge.
+__device__ __forceinline__ bool step_walker(Walker& w, bool act) {
+  vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
+  const bool mv = act && w.gx < -w.h;
   w.rel += mv ? w.dir : 0;
-  w.hidx += mv ? w.dmin : 0;
+  w.hb += mv ? w.dmin : 0;
+  w.inc ^= mv ? (w.fmaj ^ 0x10001u) : 0u;
   w.yb += mv ? w.dys : 0.f;
   w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-  vote_if(B, mv && (unsigned)w.rel <= (unsigned)w.span, w.hidx);
-  return mv && (w.gx + w.h < 0.f) && w.rel != w.rlim;
+  vote_if(mv && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
+  return mv && w.gx < -w.h;
 }
 
-// Remaining crossings of a step (slopes above one cell per step; rare).
-__device__ __forceinline__ void more_crossings(const Band& B, Walker& w) {
-  while (w.gx + w.h < 0.f && w.rel != w.rlim) {
+// Remaining crossings of a step (slopes above one cell per step; rare). Bounded by the
+// grid edge.
+__device__ __forceinline__ void more_crossings(Walker& w) {
+  while (w.gx < -w.h && (w.dir > 0 ? w.rel < w.rlim : w.rel > w.rlim)) {
     w.rel += w.dir;
-    w.hidx += w.dmin;
+    w.hb += w.dmin;
+    w.inc ^= w.fmaj ^ 0x10001u;
     w.yb += w.dys;
     w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-    vote_if(B, (unsigned)w.rel <= (unsigned)w.span, w.hidx);
+    vote_if((unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
   }
 }
 
 __device__ __forceinline__ void advance(Walker& w, float step) {
-  w.hidx += w.dmaj;
+  w.hb += w.dmaj;
+  w.inc ^= w.fmaj;
   w.xe += step;
   w.gx = w.xe * fmaf(w.d3, w.xe, w.dM2);
 }
 
 // Phase B (the whole warp, its batch of circles). The pieces of all circles are cut into
-// segments of at most kSeg major steps and dealt out in rounds, two segments per lane, so
-// that every lane decodes its segments and solves their start quadratics at the same time
-// and walks two independent segments in lock step.
+// segments of at most kSeg major steps and dealt out in rounds, kWalkers segments per lane,
+// so that every lane decodes its segments and solves their start quadratics at the same time
+// and walks independent segments in lock step.
 __device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
                                            int lane) {
-  for (int base = 0; base < total_segs; base += 64) {
-    Walker a, b;
-    start_walker(B, tab, total_segs, base + lane, a);
-    start_walker(B, tab, total_segs, base + 32 + lane, b);
-    const int rounds = __reduce_max_sync(kFull, (unsigned)max(a.len, b.len));
+  for (int base = 0; base < total_segs; base += 32 * kWalkers) {
+    Walker w[kWalkers];
+    int longest = 0;
+#pragma unroll
+    for (int j = 0; j < kWalkers; ++j) {
+      start_walker(B, tab, total_segs, base + 32 * j + lane, w[j]);
+      longest = max(longest, w[j].len);
+    }
+    const int rounds = __reduce_max_sync(kFull, (unsigned)longest);
     for (int i = 0; i < rounds; ++i) {
-      const bool more_a = step_walker(B, a, i < a.len);
-      const bool more_b = step_walker(B, b, i < b.len);
-      if (__any_sync(kFull, more_a || more_b)) {
-        if (more_a) more_crossings(B, a);
-        if (more_b) more_crossings(B, b);
+      bool more[kWalkers], any = false;
+#pragma unroll
+      for (int j = 0; j < kWalkers; ++j) {
+        more[j] = step_walker(w[j], i < w[j].len);
+        any |= more[j];
       }
-      advance(a, B.step);
-      advance(b, B.step);
+      if (__any_sync(kFull, any)) {
+#pragma unroll
+        for (int j = 0; j < kWalkers; ++j)
+          if (more[j]) more_crossings(w[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < kWalkers; ++j) advance(w[j], B.step);
     }
   }
 }
