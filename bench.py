@@ -18,6 +18,7 @@ workload: the vote does not need any exchange, so there is no collective on the 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sprot", choices=["sprot", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1500,
+    ap.add_argument("--cpu-sample", type=int, default=10000,
                     help="correspondences of the oracle baseline sample")
     return ap.parse_args()
 
@@ -154,6 +155,21 @@ class ClockSampler:
 # the headline workload on the GPU
 # ---------------------------------------------------------------------------------------
 
+def vote_traffic():
+    """DRAM bytes (read + write) per launch of the axis-vote kernel from the committed ncu
+    capture, or None when the kernel source has changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", "axis_vote_traffic.json")
+    src = os.path.join(ROOT, "paper_2502_06337_gb300", "csrc", "vote_walk.cu")
+    try:
+        rec = json.load(open(prof))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256") != digest:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def headline_problem(seed):
     from paper_2502_06337_gb300 import synth
 
@@ -252,7 +268,7 @@ def run_sprot(args):
     roofline = {
         "bound": "alu",
         "resource": "shared-memory atomic unit (red.shared.add.u32 per voted cell)",
-        "kernel": "k_axis_vote",
+        "kernel": "k_axis_vote_walk",
         "achieved": achieved / 1e9,
         "peak": atomic_peak / 1e9,
         "unit": "Gatom/s",
@@ -263,12 +279,7 @@ def run_sprot(args):
         "kernel_share_of_step": vote_s * 1e3 / (sum(step_ms) / len(step_ms)),
         "traffic": None,
     }
-    prof = os.path.join(ROOT, "profiles", "axis_vote_traffic.json")
-    if os.path.exists(prof):
-        try:
-            roofline["traffic"] = json.load(open(prof)).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    roofline["traffic"] = vote_traffic()
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -62,29 +62,64 @@ __device__ __forceinline__ bool suppressed(const CellAxis& c, const CellAxis& p,
   return dot >= cosr * (c.N * p.N);
 }
 
-__global__ void __launch_bounds__(256)
+// Sum of the slice partials of kReduceWords accumulator words: one 16-byte column (4 words,
+// 8 cells) per thread, the S slices loaded several at a time, then the grid and the largest
+// peak key of the item.
+__global__ void __launch_bounds__(kReduceWords / 4)
     k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
   const ReduceItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
-  const int G = D.G, W = G >> 1;
+  const int G = D.G, W = G >> 1, S = D.S;
   const int64_t plane = (int64_t)G * W;
   unsigned long long best = 0;
-  for (int64_t w = I.w0 + threadIdx.x; w < I.w1; w += blockDim.x) {
-    uint32_t lo = 0, hi = 0;
-    const uint32_t* p = D.partial + w;
-    for (int s = 0; s < D.S; ++s) {
-      uint32_t v = __ldg(p + (int64_t)s * plane);
-      lo += v & 0xffffu;
-      hi += v >> 16;
+  const int64_t w = I.w0 + 4 * threadIdx.x;  // words w .. w+3 lie in one row (W % 4 == 0)
+  if (w < I.w1) {
+    uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint4* p = reinterpret_cast<const uint4*>(D.partial + w);
+    const int64_t stride = plane / 4;
+    int s = 0;
+    for (; s + 4 <= S; s += 4) {
+      uint4 v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = __ldcs(p + (s + t) * stride);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        c[0] += v[t].x & 0xffffu;
+        c[1] += v[t].x >> 16;
+        c[2] += v[t].y & 0xffffu;
+        c[3] += v[t].y >> 16;
+        c[4] += v[t].z & 0xffffu;
+        c[5] += v[t].z >> 16;
+        c[6] += v[t].w & 0xffffu;
+        c[7] += v[t].w >> 16;
+      }
+    }
+    for (; s < S; ++s) {
+      const uint4 v = __ldcs(p + s * stride);
+      c[0] += v.x & 0xffffu;
+      c[1] += v.x >> 16;
+      c[2] += v.y & 0xffffu;
+      c[3] += v.y >> 16;
+      c[4] += v.z & 0xffffu;
+      c[5] += v.z >> 16;
+      c[6] += v.w & 0xffffu;
+      c[7] += v.w >> 16;
     }
     // word j of a row holds columns 2j (low half) and 2j + 1 (high half)
-    int row = (int)(w / W), c = 2 * (int)(w - (int64_t)row * W);
-    D.grid[(int64_t)row * G + c] = lo;
-    D.grid[(int64_t)row * G + c + 1] = hi;
-    unsigned long long k1 = peak_key(lo, (uint32_t)(row * G + c));
-    unsigned long long k2 = peak_key(hi, (uint32_t)(row * G + c + 1));
-    best = k1 > best ? k1 : best;
-    best = k2 > best ? k2 : best;
+    const int row = (int)(w / W), col = 2 * (int)(w - (int64_t)row * W);
+    uint32_t* g = D.grid + (int64_t)row * G + col;
+    if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
+      reinterpret_cast<uint4*>(g)[0] = make_uint4(c[0], c[1], c[2], c[3]);
+      reinterpret_cast<uint4*>(g)[1] = make_uint4(c[4], c[5], c[6], c[7]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) g[t] = c[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const unsigned long long k = peak_key(c[t], (uint32_t)(row * G + col + t));
+      best = k > best ? k : best;
+    }
   }
   best = block_max_u64(best);
   if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[0], best);
@@ -335,11 +370,15 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Block sum of acc[kMaxK][10] into out (fixed order: warps in index order). All threads call.
-__device__ void block_sums(double (*acc)[10], int kf, double* out) {
+// Block sum of acc[K][10] into out[kf][10] (fixed order: warps in index order). All threads
+// call; the rotation loop is unrolled so that acc stays in registers.
+template <int K>
+__device__ __forceinline__ void block_sums(double (&acc)[K][10], int kf, double* out) {
   __shared__ double s[kStreamThreads / 32][10];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int a = 0; a < kf; ++a) {
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    if (a >= kf) break;
 #pragma unroll
     for (int t = 0; t < 10; ++t) {
       double v = warp_sum_d(acc[a][t]);
@@ -355,8 +394,11 @@ __device__ void block_sums(double (*acc)[10], int kf, double* out) {
   }
 }
 
-__device__ __forceinline__ void add_qpT(double* acc, const float* p, const float* q) {
-  double p0 = p[0], p1 = p[1], p2 = p[2], q0 = q[0], q1 = q[1], q2 = q[2];
+// q p^T of pair i added to acc[0..8] in FP64 (the float32 products are exact in FP64).
+__device__ __forceinline__ void add_qpT(double* acc, const float* __restrict__ P,
+                                        const float* __restrict__ Q, int64_t i) {
+  const double p0 = __ldg(P + 3 * i), p1 = __ldg(P + 3 * i + 1), p2 = __ldg(P + 3 * i + 2);
+  const double q0 = __ldg(Q + 3 * i), q1 = __ldg(Q + 3 * i + 1), q2 = __ldg(Q + 3 * i + 2);
   acc[0] = fma(q0, p0, acc[0]);
   acc[1] = fma(q0, p1, acc[1]);
   acc[2] = fma(q0, p2, acc[2]);
@@ -366,8 +408,58 @@ __device__ __forceinline__ void add_qpT(double* acc, const float* p, const float
   acc[6] = fma(q2, p0, acc[6]);
   acc[7] = fma(q2, p1, acc[7]);
   acc[8] = fma(q2, p2, acc[8]);
-  acc[9] += 1.0;
 }
+
+// Per-warp queues of selected pairs, one per rotation. FP64 arithmetic runs on GB300 at a
+// small fraction of the FP32 rate and costs the same per warp instruction whatever the number
+// of active lanes, so the sums are taken over full warps of selected pairs: a pair is queued
+// (as its offset in the work item) when selected, and each time a queue holds 32 pairs the
+// whole warp adds them.
+template <int K>
+struct PairQueues {
+  double acc[K][10];
+  int len[K];    // warp-uniform queue lengths
+  int total[K];  // warp-uniform counts of selected pairs
+  int* q;        // this warp's queues: [K][64] in shared memory
+
+  __device__ __forceinline__ void init(int* warp_q) {
+    q = warp_q;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      len[a] = total[a] = 0;
+#pragma unroll
+      for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+    }
+  }
+  // Queue pair i0 + off for rotation a if sel (called by the whole warp with a uniform a).
+  __device__ __forceinline__ void push(int A, bool sel, int off, const InstDev& D, int64_t i0, int lane) {
+    const unsigned bal = __ballot_sync(kFull, sel);
+    if (!bal) return;
+    const int pos = len[A] + __popc(bal & ((1u << lane) - 1u));
+    if (sel) q[A * 64 + pos] = off;
+    len[A] += __popc(bal);
+    total[A] += __popc(bal);
+    if (len[A] >= 32) {
+      __syncwarp();
+      add_qpT(acc[A], D.P, D.Q, i0 + q[A * 64 + lane]);
+      const int rest = len[A] - 32;
+      const int moved = lane < rest ? q[A * 64 + 32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) q[A * 64 + lane] = moved;
+      __syncwarp();
+      len[A] = rest;
+    }
+  }
+  __device__ __forceinline__ void flush(const InstDev& D, int64_t i0, int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+      if (lane < len[a]) add_qpT(acc[a], D.P, D.Q, i0 + q[a * 64 + lane]);
+    // the pair count travels in slot 9, once per warp
+#pragma unroll
+    for (int a = 0; a < K; ++a) acc[a][9] = lane == 0 ? (double)total[a] : 0.0;
+  }
+};
 
 template <int K>
 __global__ void __launch_bounds__(kStreamThreads)
@@ -376,37 +468,39 @@ __global__ void __launch_bounds__(kStreamThreads)
   const InstDev& D = insts[I.inst];
   __shared__ int bhat[kMaxK];
   __shared__ int s_found;
+  __shared__ int queues[kStreamThreads / 32][K * 64];
   if (threadIdx.x == 0) s_found = *D.n_found;
   __syncthreads();
   const int kf = s_found;
   if (threadIdx.x < kf) bhat[threadIdx.x] = D.rot[threadIdx.x].angle_bin;
   __syncthreads();
-  double acc[K][10];
-  for (int a = 0; a < K; ++a)
-    for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  PairQueues<K> pq;
+  pq.init(queues[wp]);
   const int J = D.J;
-  for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
-    for (int a = 0; a < kf; ++a) {
-      int b = D.bins[(int64_t)a * D.n + i];
-      bool in = false;
-      if (b >= 0) {
-        int dd = b - bhat[a];
-        if (dd < 0) dd = -dd;
-        dd = min(dd, J - dd);
-        in = dd <= D.window;
-      }
-      if (D.vote_set) D.vote_set[(int64_t)a * D.n + i] = in;
-      if (in) {
-        float p[3] = {D.P[3 * i], D.P[3 * i + 1], D.P[3 * i + 2]};
-        float q[3] = {D.Q[3 * i], D.Q[3 * i + 1], D.Q[3 * i + 2]};
-        // the rotation index is runtime; keep acc in registers by unrolled selection
+  // each warp takes 32 consecutive pairs per iteration
+  for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
+    const int64_t i = base + lane;
+    const bool valid = i < I.i1;
 #pragma unroll
-        for (int t = 0; t < K; ++t)
-          if (t == a) add_qpT(acc[t], p, q);
+    for (int a = 0; a < K; ++a) {
+      if (a >= kf) break;
+      bool in = false;
+      if (valid) {
+        const int b = D.bins[(int64_t)a * D.n + i];
+        if (b >= 0) {
+          int dd = b - bhat[a];
+          if (dd < 0) dd = -dd;
+          dd = min(dd, J - dd);
+          in = dd <= D.window;
+        }
+        if (D.vote_set) D.vote_set[(int64_t)a * D.n + i] = in;
       }
+      pq.push(a, in, (int)(i - I.i0), D, I.i0, lane);
     }
   }
-  block_sums(acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
+  pq.flush(D, I.i0, lane);
+  block_sums(pq.acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
 }
 
 // Residual labels against every R_init (float32 test of ||q - R p||^2 <= tau^2) and the
@@ -418,40 +512,46 @@ __global__ void __launch_bounds__(kStreamThreads)
   const InstDev& D = insts[I.inst];
   __shared__ float Rf[kMaxK][9];
   __shared__ int s_found;
+  __shared__ int queues[kStreamThreads / 32][K * 64];
   if (threadIdx.x == 0) s_found = *D.n_found;
   __syncthreads();
   const int kf = s_found;
   if (threadIdx.x < kf * 9) Rf[threadIdx.x / 9][threadIdx.x % 9] = D.rot[threadIdx.x / 9].R_init_f[threadIdx.x % 9];
   __syncthreads();
-  double acc[K][10];
-  for (int a = 0; a < K; ++a)
-    for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  PairQueues<K> pq;
+  pq.init(queues[wp]);
   const float tau2 = D.tau * D.tau;
-  for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
-    float p[3] = {D.P[3 * i], D.P[3 * i + 1], D.P[3 * i + 2]};
-    float q[3] = {D.Q[3 * i], D.Q[3 * i + 1], D.Q[3 * i + 2]};
+  for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
+    const int64_t i = base + lane;
+    const bool valid = i < I.i1;
     int lab = -1;
-    float best = CUDART_INF_F;
-    for (int a = 0; a < kf; ++a) {
-      const float* R = Rf[a];
-      float e0 = q[0] - fmaf(R[0], p[0], fmaf(R[1], p[1], R[2] * p[2]));
-      float e1 = q[1] - fmaf(R[3], p[0], fmaf(R[4], p[1], R[5] * p[2]));
-      float e2 = q[2] - fmaf(R[6], p[0], fmaf(R[7], p[1], R[8] * p[2]));
-      float r2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-      if (r2 <= tau2 && r2 < best) {
-        best = r2;
-        lab = a;
+    if (valid) {
+      const float p0 = __ldg(D.P + 3 * i), p1 = __ldg(D.P + 3 * i + 1), p2 = __ldg(D.P + 3 * i + 2);
+      const float q0 = __ldg(D.Q + 3 * i), q1 = __ldg(D.Q + 3 * i + 1), q2 = __ldg(D.Q + 3 * i + 2);
+      float best = CUDART_INF_F;
+      for (int a = 0; a < kf; ++a) {
+        const float* R = Rf[a];
+        const float e0 = q0 - fmaf(R[0], p0, fmaf(R[1], p1, R[2] * p2));
+        const float e1 = q1 - fmaf(R[3], p0, fmaf(R[4], p1, R[5] * p2));
+        const float e2 = q2 - fmaf(R[6], p0, fmaf(R[7], p1, R[8] * p2));
+        const float r2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        if (r2 <= tau2 && r2 < best) {
+          best = r2;
+          lab = a;
+        }
       }
+      if (D.labels) D.labels[i] = lab;
+      if (D.mask) D.mask[i] = lab >= 0;
     }
-    if (D.labels) D.labels[i] = lab;
-    if (D.mask) D.mask[i] = lab >= 0;
-    if (lab >= 0) {
 #pragma unroll
-      for (int t = 0; t < K; ++t)
-        if (t == lab) add_qpT(acc[t], p, q);
+    for (int a = 0; a < K; ++a) {
+      if (a >= kf) break;
+      pq.push(a, lab == a, (int)(i - I.i0), D, I.i0, lane);
     }
   }
-  block_sums(acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
+  pq.flush(D, I.i0, lane);
+  block_sums(pq.acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
 }
 
 // ---- FP64 rotation from the sums (Horn's unit-quaternion method) --------------------------
@@ -565,28 +665,175 @@ __device__ bool polar_rotation(const double* M, double* R) {
   return true;
 }
 
-// phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One warp per
-// (instance, rotation); the item partials are summed in a fixed order.
-__global__ void k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
+// Rotation matrix of a unit quaternion (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_to_rot(const double* q, double* R) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = w * w + x * x - y * y - z * z;
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = w * w - x * x + y * y - z * z;
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = w * w - x * x - y * y + z * z;
+}
+
+// Start value of the polar factor: scaled Newton iteration in float32 on X (|X|_F = 1,
+// det X > 0), then Shepperd's quaternion of the result (largest of the trace and the diagonal
+// chooses the stable formula). Returns false if float32 cannot carry the iteration.
+__device__ bool polar_start_f32(const double* Xd, double* q) {
+  float X[9];
+  for (int t = 0; t < 9; ++t) X[t] = (float)Xd[t];
+  for (int it = 0; it < 30; ++it) {
+    const float C[9] = {X[4] * X[8] - X[5] * X[7], X[5] * X[6] - X[3] * X[8], X[3] * X[7] - X[4] * X[6],
+                        X[2] * X[7] - X[1] * X[8], X[0] * X[8] - X[2] * X[6], X[1] * X[6] - X[0] * X[7],
+                        X[1] * X[5] - X[2] * X[4], X[2] * X[3] - X[0] * X[5], X[0] * X[4] - X[1] * X[3]};
+    const float det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    float xn = 0.f, cn = 0.f;
+    for (int t = 0; t < 9; ++t) {
+      xn += X[t] * X[t];
+      cn += C[t] * C[t];
+    }
+    if (!(det > 0.f) || !(xn > 0.f)) return false;
+    const float g = sqrtf(sqrtf(cn / xn) / det);
+    const float a = 0.5f * g, b = 0.5f / (g * det);
+    float diff = 0.f;
+    for (int t = 0; t < 9; ++t) {
+      const float y = fmaf(a, X[t], b * C[t]);
+      diff += (y - X[t]) * (y - X[t]);
+      X[t] = y;
+    }
+    if (diff < 1e-12f) break;
+  }
+  const float tr = X[0] + X[4] + X[8];
+  float w, x, y, z;
+  if (tr >= X[0] && tr >= X[4] && tr >= X[8]) {
+    w = 0.5f * sqrtf(fmaxf(1.f + tr, 0.f));
+    const float f = 0.25f / w;
+    x = (X[7] - X[5]) * f;
+    y = (X[2] - X[6]) * f;
+    z = (X[3] - X[1]) * f;
+  } else if (X[0] >= X[4] && X[0] >= X[8]) {
+    x = 0.5f * sqrtf(fmaxf(1.f + X[0] - X[4] - X[8], 0.f));
+    const float f = 0.25f / x;
+    w = (X[7] - X[5]) * f;
+    y = (X[1] + X[3]) * f;
+    z = (X[2] + X[6]) * f;
+  } else if (X[4] >= X[8]) {
+    y = 0.5f * sqrtf(fmaxf(1.f - X[0] + X[4] - X[8], 0.f));
+    const float f = 0.25f / y;
+    w = (X[2] - X[6]) * f;
+    x = (X[1] + X[3]) * f;
+    z = (X[5] + X[7]) * f;
+  } else {
+    z = 0.5f * sqrtf(fmaxf(1.f - X[0] - X[4] + X[8], 0.f));
+    const float f = 0.25f / z;
+    w = (X[3] - X[1]) * f;
+    x = (X[2] + X[6]) * f;
+    y = (X[5] + X[7]) * f;
+  }
+  const double qn = sqrt((double)w * w + (double)x * x + (double)y * y + (double)z * z);
+  if (!(qn > 0.5)) return false;
+  q[0] = w / qn;
+  q[1] = x / qn;
+  q[2] = y / qn;
+  q[3] = z / qn;
+  return true;
+}
+
+// Polar factor of X (det X > 0) refined in FP64 from the quaternion q of a nearby rotation U.
+// The polar factor is the rotation U with U^T X symmetric. Writing the correction as
+// U exp([w]x) and keeping first-order terms, with Y = U^T X and H its symmetric part,
+// [w]x H + H [w]x = [(tr(H) I - H) w]x gives (tr(H) I - H) w = (Y21 - Y12, Y02 - Y20,
+// Y10 - Y01). The step is applied as the Cayley rotation of w, i.e. q <- q (1, w/2) / norm,
+// so U stays orthogonal to rounding; convergence is quadratic, and from a float32 start two or
+// three steps reach the rounding floor. Returns false if the linear system is not positive
+// definite or the last correction is not below 1e-11 (the iteration did not settle).
+__device__ bool polar_refine_f64(const double* X, double* q, double* R) {
+  double n2 = 1.0;
+  for (int it = 0; it < 4 && n2 >= 1e-30; ++it) {
+    quat_to_rot(q, R);
+    double Y[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Y[3 * i + j] = R[i] * X[j] + R[3 + i] * X[3 + j] + R[6 + i] * X[6 + j];
+    const double v0 = Y[7] - Y[5], v1 = Y[2] - Y[6], v2 = Y[3] - Y[1];
+    const double h01 = 0.5 * (Y[1] + Y[3]), h02 = 0.5 * (Y[2] + Y[6]), h12 = 0.5 * (Y[5] + Y[7]);
+    const double a00 = Y[4] + Y[8], a11 = Y[0] + Y[8], a22 = Y[0] + Y[4];
+    const double a01 = -h01, a02 = -h02, a12 = -h12;
+    const double c00 = a11 * a22 - a12 * a12, c11 = a00 * a22 - a02 * a02, c22 = a00 * a11 - a01 * a01;
+    const double c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11, c12 = a01 * a02 - a00 * a12;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(det > 0.0) || !(a00 > 0.0)) return false;
+    const double inv = 0.5 / det;  // half of w: the Cayley vector
+    const double w0 = (c00 * v0 + c01 * v1 + c02 * v2) * inv;
+    const double w1 = (c01 * v0 + c11 * v1 + c12 * v2) * inv;
+    const double w2 = (c02 * v0 + c12 * v1 + c22 * v2) * inv;
+    n2 = w0 * w0 + w1 * w1 + w2 * w2;
+    const double a = q[0], b = q[1], c = q[2], d = q[3];
+    double t0 = a - b * w0 - c * w1 - d * w2;
+    double t1 = a * w0 + b + c * w2 - d * w1;
+    double t2 = a * w1 - b * w2 + c + d * w0;
+    double t3 = a * w2 + b * w1 - c * w0 + d;
+    const double rn = 1.0 / sqrt(t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3);
+    q[0] = t0 * rn;
+    q[1] = t1 * rn;
+    q[2] = t2 * rn;
+    q[3] = t3 * rn;
+  }
+  quat_to_rot(q, R);
+  return n2 < 2.5e-23;  // half the last correction below 5e-12
+}
+
+// phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One block per
+// (instance, rotation): the item partials are summed in a fixed order (thread t takes items
+// t, t + 256, ...; then warps, then the block), and thread 0 solves for the rotation.
+__global__ void __launch_bounds__(256) k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
   const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
   const InstDev& D = insts[inst];
   if (a >= *D.n_found) return;
-  const int lane = threadIdx.x;
   double s[10];
+#pragma unroll
   for (int t = 0; t < 10; ++t) s[t] = 0.0;
   const double* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
-  for (int it = lane; it < D.n_items; it += 32)
-    for (int t = 0; t < 10; ++t) s[t] += base[(int64_t)it * D.k * 10 + t];
-  for (int t = 0; t < 10; ++t) s[t] = warp_sum_d(s[t]);
-  if (lane != 0) return;
+  for (int it = threadIdx.x; it < D.n_items; it += blockDim.x) {
+    const double* src = base + (int64_t)it * D.k * 10;
+#pragma unroll
+    for (int t = 0; t < 10; ++t) s[t] += src[t];
+  }
+  __shared__ double red[8][10];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 10; ++t) {
+    const double v = warp_sum_d(s[t]);
+    if (l == 0) red[w][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int t = 0; t < 10; ++t) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i][t];
+    s[t] = v;
+  }
   DevRot& R = D.rot[a];
   double out[9];
-  uint32_t cnt = (uint32_t)s[9];
+  const uint32_t cnt = (uint32_t)s[9];
   if (cnt == 0) {
     const double* fb = phase == 0 ? R.R_vote : R.R_init;
     for (int t = 0; t < 9; ++t) out[t] = fb[t];
-  } else if (!polar_rotation(s, out)) {
-    horn_rotation(s, out);  // reflecting or rank-deficient sums
+  } else {
+    // M / |M|_F has the same polar factor; det > 0 (beyond rounding) selects the polar path
+    double n2 = 0.0;
+    for (int t = 0; t < 9; ++t) n2 += s[t] * s[t];
+    double X[9];
+    const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+    for (int t = 0; t < 9; ++t) X[t] = s[t] * inv;
+    const double det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
+                       X[2] * (X[3] * X[7] - X[4] * X[6]);
+    double q[4];
+    const bool ok = det > 1e-9 && polar_start_f32(X, q) && polar_refine_f64(X, q, out);
+    if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
   }
   if (phase == 0) {
     for (int t = 0; t < 9; ++t) {
@@ -628,7 +875,7 @@ void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, 
 
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st) {
-  k_grid_reduce<<<n_items, 256, 0, st>>>(items, insts);
+  k_grid_reduce<<<n_items, kReduceWords / 4, 0, st>>>(items, insts);
   launches_add(1);
 }
 
@@ -674,7 +921,7 @@ void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* in
 }
 
 void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st) {
-  k_kabsch<<<m * max_k, 32, 0, st>>>(insts, max_k, phase);
+  k_kabsch<<<m * max_k, 256, 0, st>>>(insts, max_k, phase);
   launches_add(1);
 }
 

@@ -274,8 +274,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
       for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
     }
     int64_t words = (int64_t)ip.G * (ip.G / 2);
-    for (int64_t w0 = 0; w0 < words; w0 += 1024)
-      ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+    for (int64_t w0 = 0; w0 < words; w0 += kReduceWords)
+      ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + kReduceWords, words)});
     ip.chunk = stream_chunk(pb.n);
     ip.item0 = (int)sitems.size();
     for (int64_t a = 0; a < pb.n; a += ip.chunk)
@@ -476,7 +476,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
     for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
   std::vector<ReduceItem> rit;
   int64_t words = (int64_t)G * (G / 2);
-  for (int64_t w0 = 0; w0 < words; w0 += 1024) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+  for (int64_t w0 = 0; w0 < words; w0 += kReduceWords) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + kReduceWords, words)});
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
   size_t o_inst = take(sizeof(InstDev)), o_vit = take(sizeof(VoteItem) * vit.size()),
@@ -529,7 +529,7 @@ int select_peaks(const uint32_t* grid, int G, int k, float nms_deg, int32_t* cel
   std::lock_guard<std::mutex> lock(ws->mu);
   std::vector<ReduceItem> rit;
   int64_t words = (int64_t)G * (G / 2);
-  for (int64_t w0 = 0; w0 < words; w0 += 1024) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + 1024, words)});
+  for (int64_t w0 = 0; w0 < words; w0 += kReduceWords) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + kReduceWords, words)});
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1)); return o; };
   size_t o_inst = take(sizeof(InstDev)), o_rit = take(sizeof(ReduceItem) * rit.size());

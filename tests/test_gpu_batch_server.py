@@ -1,0 +1,134 @@
+"""The batched and served forms against the plain solve and the FP64 oracle (gpu).
+
+A batch of uneven instances solved in one launch sequence must give, per instance, the same
+integer results (cells, bins, counts, sets) as solving that instance alone, and FP64
+rotations equal to rounding; the served form must give every request the result it has
+alone, whatever else is in flight."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_06337_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+INT_KEYS = ("cell", "bin", "axis_votes", "angle_votes", "n_vote_set", "n_inliers", "n_degenerate")
+
+
+def _same(a, b, tol=1e-12):
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        for key in INT_KEYS:
+            assert x[key] == y[key], (key, x[key], y[key])
+        assert parity.rot_diff(x["R"], y["R"]) < tol
+        assert parity.rot_diff(x["R_init"], y["R_init"]) < tol
+
+
+def _instances():
+    """Uneven instances: sizes from 1 to 60k, outlier rates 30-95 %, one with three
+    rotations, one whose pairs are all degenerate (no axis), fixed and autotuned grids."""
+    specs = [
+        dict(n=700, fr=(0.5,), sigma=0.01, seed=11, grid=128, k=1),
+        dict(n=4099, fr=(0.3,), sigma=0.005, seed=12, grid=0, k=1),
+        dict(n=60000, fr=(0.05,), sigma=0.01, seed=13, grid=0, k=1),
+        dict(n=20000, fr=(0.2, 0.2, 0.2), sigma=0.01, seed=14, grid=256, k=3),
+        dict(n=1, fr=(1.0,), sigma=0.0, seed=15, grid=64, k=1),
+        dict(n=300, fr=(0.7,), sigma=0.02, seed=16, grid=16, k=2),
+    ]
+    out = []
+    for s in specs:
+        pb = synth.make_problem(s["n"], s["fr"], s["sigma"], seed=s["seed"])
+        out.append((pb, s))
+    # all pairs degenerate: p = q
+    P = synth.make_problem(50, (0.0,), 0.0, seed=17).P
+    out.append((synth.Problem(P=P, Q=P.copy(), rotations=[], truth=np.full(50, -1), sigma=0.0,
+                              seed=17), dict(n=50, grid=32, k=1)))
+    return out
+
+
+def _params(B, s, tau=0.05):
+    return B.make_params(grid=s["grid"], angle_bins=360, k=s["k"], nms_deg=2.0, tau=tau)
+
+
+def test_batch_matches_single_solves(lib):
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    inst = _instances()
+    dev = [(torch.from_numpy(pb.P).cuda(), torch.from_numpy(pb.Q).cuda()) for pb, _ in inst]
+    batch = [(P, Q, _params(B, s)) for (P, Q), (_, s) in zip(dev, inst)]
+    res, grids = B.estimate_batch(batch)
+    for i, ((P, Q), (pb, s)) in enumerate(zip(dev, inst)):
+        if s["grid"]:
+            assert grids[i] == s["grid"]
+        else:
+            assert grids[i] == lib.sprot_autotune_grid(pb.n)
+        prm = B.make_params(grid=grids[i], angle_bins=360, k=s["k"], nms_deg=2.0, tau=0.05)
+        alone = B.estimate_rotations(P, Q, prm, allow_noaxis=True)
+        _same(res[i], alone)
+    assert res[-1] == []  # the all-degenerate instance finds no axis and does not disturb the rest
+
+
+def test_batch_small_instances_match_oracle(lib):
+    """End to end against the oracle's solve on the small instances of the batch (same grid):
+    same cells and bins and rotations within the estimator's 1e-5 rad."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    inst = [x for x in _instances() if x[1]["n"] in (700, 300, 1)]
+    batch = [(torch.from_numpy(pb.P).cuda(), torch.from_numpy(pb.Q).cuda(), _params(B, s))
+             for pb, s in inst]
+    res, grids = B.estimate_batch(batch)
+    for (pb, s), r, G in zip(inst, res, grids):
+        want = oracle.solve(pb.P, pb.Q, G, 360, k=s["k"], nms_deg=2.0, tau=0.05)
+        assert [x["cell"] for x in r] == [(row, col) for row, col, _ in want["peaks"]]
+        for a, x in enumerate(r):
+            assert x["bin"] == want["rotations"][a]["bin"]
+            assert parity.rot_diff(x["R"], want["rotations"][a]["R"]) < parity.E2E_ROT_TOL
+
+
+def test_server_results_equal_alone(lib):
+    """Requests of different sizes and rotation counts submitted together: each result is
+    the one the request gets alone (same integers, FP64 rotations equal to rounding)."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    inst = [x for x in _instances() if x[1]["n"] > 1]
+    alone = []
+    for pb, s in inst:
+        P = torch.from_numpy(pb.P).cuda()
+        Q = torch.from_numpy(pb.Q).cuda()
+        alone.append(B.estimate_rotations(P, Q, _params(B, s), allow_noaxis=True))
+    with B.Server(2 << 30, max_batch=8) as srv:
+        for rep in range(3):
+            tickets = [srv.submit(pb.P, pb.Q, _params(B, s)) for pb, s in inst]
+            got = [srv.wait(t) for t in tickets]
+            for (pb, s), g, a in zip(inst, got, alone):
+                if a:
+                    assert g["status"] == 0
+                else:
+                    assert g["status"] == B.E_NOAXIS
+                _same(g["rotations"], a)
+                assert g["t_submit_ms"] <= g["t_admit_ms"] <= g["t_done_ms"]
+
+
+def test_server_admission_and_invalid_requests(lib):
+    from paper_2502_06337_gb300 import binding as B
+
+    pb = synth.make_problem(100_000, (0.2,), 0.01, seed=21)
+    with B.Server(1 << 20, max_batch=4) as srv:  # 1 MB budget: the request can never fit
+        st, _ = srv.try_submit(pb.P, pb.Q, B.make_params(grid=256, angle_bins=360))
+        assert st == B.E_NOMEM
+        st, _ = srv.try_submit(pb.P, pb.Q, B.make_params(grid=24, angle_bins=360))  # not a power of two
+        assert st == B.E_INVAL
+        small = synth.make_problem(200, (0.5,), 0.01, seed=22)
+        t = srv.submit(small.P, small.Q, B.make_params(grid=16, angle_bins=90))
+        r = srv.wait(t)
+        assert r["status"] == 0 and len(r["rotations"]) == 1
+        with pytest.raises(B.SprotError) as e:
+            srv.wait(t + 1000)  # no such ticket
+        assert e.value.status == B.E_INVAL
