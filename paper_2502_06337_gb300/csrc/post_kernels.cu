@@ -742,48 +742,57 @@ __device__ bool polar_start_f32(const double* Xd, double* q) {
   return true;
 }
 
-// Polar factor of X (det X > 0) refined in FP64 from the quaternion q of a nearby rotation U.
-// The polar factor is the rotation U with U^T X symmetric. Writing the correction as
-// U exp([w]x) and keeping first-order terms, with Y = U^T X and H its symmetric part,
-// [w]x H + H [w]x = [(tr(H) I - H) w]x gives (tr(H) I - H) w = (Y21 - Y12, Y02 - Y20,
-// Y10 - Y01). The step is applied as the Cayley rotation of w, i.e. q <- q (1, w/2) / norm,
-// so U stays orthogonal to rounding; convergence is quadratic, and from a float32 start two or
-// three steps reach the rounding floor. Returns false if the linear system is not positive
-// definite or the last correction is not below 1e-11 (the iteration did not settle).
+// Polar factor of X (det X > 0) refined from the quaternion q of a nearby rotation U. The
+// polar factor is the rotation U with U^T X symmetric. Writing the correction as U exp([w]x)
+// and keeping first-order terms, with Y = U^T X and H its symmetric part,
+// [w]x H + H [w]x = [(tr(H) I - H) w]x gives (tr(H) I - H) w = v, v = (Y21 - Y12, Y02 - Y20,
+// Y10 - Y01). The step is applied as the Cayley rotation of w: q <- q (1, w/2). Only v (the
+// residual that the iteration drives to zero) and the quaternion are carried in FP64; H and
+// the 3 x 3 solve need no more than float32, whose relative error in w only adds a factor
+// 1 + 1e-7 cond to the quadratic convergence. q is left unnormalised until the end (a scale
+// of U scales v and H alike and leaves w unchanged). From a float32 start three steps reach
+// the FP64 rounding floor. Returns false if the system is not positive definite or the last
+// correction is not below 5e-12 (the iteration did not settle).
 __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
-  double n2 = 1.0;
-  for (int it = 0; it < 4 && n2 >= 1e-30; ++it) {
-    quat_to_rot(q, R);
-    double Y[9];
+  float Xf[9];
+  for (int t = 0; t < 9; ++t) Xf[t] = (float)X[t];
+  float n2 = 1.f;
+  for (int it = 0; it < 4 && n2 >= 1e-30f; ++it) {
+    quat_to_rot(q, R);  // |q|^2 times a rotation
+    // v in FP64
+    const double v0 = (R[2] * X[1] + R[5] * X[4] + R[8] * X[7]) - (R[1] * X[2] + R[4] * X[5] + R[7] * X[8]);
+    const double v1 = (R[0] * X[2] + R[3] * X[5] + R[6] * X[8]) - (R[2] * X[0] + R[5] * X[3] + R[8] * X[6]);
+    const double v2 = (R[1] * X[0] + R[4] * X[3] + R[7] * X[6]) - (R[0] * X[1] + R[3] * X[4] + R[6] * X[7]);
+    // H and the solve in float32
+    float Rf[9], Yf[9];
+    for (int t = 0; t < 9; ++t) Rf[t] = (float)R[t];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
-        Y[3 * i + j] = R[i] * X[j] + R[3 + i] * X[3 + j] + R[6 + i] * X[6 + j];
-    const double v0 = Y[7] - Y[5], v1 = Y[2] - Y[6], v2 = Y[3] - Y[1];
-    const double h01 = 0.5 * (Y[1] + Y[3]), h02 = 0.5 * (Y[2] + Y[6]), h12 = 0.5 * (Y[5] + Y[7]);
-    const double a00 = Y[4] + Y[8], a11 = Y[0] + Y[8], a22 = Y[0] + Y[4];
-    const double a01 = -h01, a02 = -h02, a12 = -h12;
-    const double c00 = a11 * a22 - a12 * a12, c11 = a00 * a22 - a02 * a02, c22 = a00 * a11 - a01 * a01;
-    const double c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11, c12 = a01 * a02 - a00 * a12;
-    const double det = a00 * c00 + a01 * c01 + a02 * c02;
-    if (!(det > 0.0) || !(a00 > 0.0)) return false;
-    const double inv = 0.5 / det;  // half of w: the Cayley vector
-    const double w0 = (c00 * v0 + c01 * v1 + c02 * v2) * inv;
-    const double w1 = (c01 * v0 + c11 * v1 + c12 * v2) * inv;
-    const double w2 = (c02 * v0 + c12 * v1 + c22 * v2) * inv;
+        Yf[3 * i + j] = fmaf(Rf[i], Xf[j], fmaf(Rf[3 + i], Xf[3 + j], Rf[6 + i] * Xf[6 + j]));
+    const float a00 = Yf[4] + Yf[8], a11 = Yf[0] + Yf[8], a22 = Yf[0] + Yf[4];
+    const float a01 = -0.5f * (Yf[1] + Yf[3]), a02 = -0.5f * (Yf[2] + Yf[6]), a12 = -0.5f * (Yf[5] + Yf[7]);
+    const float c00 = a11 * a22 - a12 * a12, c11 = a00 * a22 - a02 * a02, c22 = a00 * a11 - a01 * a01;
+    const float c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11, c12 = a01 * a02 - a00 * a12;
+    const float det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(det > 0.f) || !(a00 > 0.f)) return false;
+    const float inv = 0.5f / det;  // half of w: the Cayley vector
+    const float fv0 = (float)v0, fv1 = (float)v1, fv2 = (float)v2;
+    const float w0 = (c00 * fv0 + c01 * fv1 + c02 * fv2) * inv;
+    const float w1 = (c01 * fv0 + c11 * fv1 + c12 * fv2) * inv;
+    const float w2 = (c02 * fv0 + c12 * fv1 + c22 * fv2) * inv;
     n2 = w0 * w0 + w1 * w1 + w2 * w2;
+    // q <- q (1, w) in FP64
     const double a = q[0], b = q[1], c = q[2], d = q[3];
-    double t0 = a - b * w0 - c * w1 - d * w2;
-    double t1 = a * w0 + b + c * w2 - d * w1;
-    double t2 = a * w1 - b * w2 + c + d * w0;
-    double t3 = a * w2 + b * w1 - c * w0 + d;
-    const double rn = 1.0 / sqrt(t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3);
-    q[0] = t0 * rn;
-    q[1] = t1 * rn;
-    q[2] = t2 * rn;
-    q[3] = t3 * rn;
+    const double x0 = w0, x1 = w1, x2 = w2;
+    q[0] = a - b * x0 - c * x1 - d * x2;
+    q[1] = a * x0 + b + c * x2 - d * x1;
+    q[2] = a * x1 - b * x2 + c + d * x0;
+    q[3] = a * x2 + b * x1 - c * x0 + d;
   }
+  const double rn = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int t = 0; t < 4; ++t) q[t] *= rn;
   quat_to_rot(q, R);
-  return n2 < 2.5e-23;  // half the last correction below 5e-12
+  return n2 < 2.5e-23f;
 }
 
 // phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One block per

@@ -206,6 +206,37 @@ __device__ void prepare(const Band& B, float d1, float d2, float d3, Prepared& S
   }
 }
 
+// Raw p and q of pair i.
+__device__ __forceinline__ void load_pair(const float* __restrict__ P, const float* __restrict__ Q,
+                                          int64_t i, float* r) {
+  r[0] = __ldg(P + 3 * i);
+  r[1] = __ldg(P + 3 * i + 1);
+  r[2] = __ldg(P + 3 * i + 2);
+  r[3] = __ldg(Q + 3 * i);
+  r[4] = __ldg(Q + 3 * i + 1);
+  r[5] = __ldg(Q + 3 * i + 2);
+}
+
+// p - q from raw values, scaled by a power of two so that max |d_k| is in [1, 2), signed so
+// d3 >= 0; false for a degenerate pair.
+__device__ __forceinline__ bool circle_from(const float* r, float& d1, float& d2, float& d3) {
+  d1 = r[0] - r[3];
+  d2 = r[1] - r[4];
+  d3 = r[2] - r[5];
+  const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
+  if (m == 0.f) return false;
+  const int e = ilogbf(m);
+  d1 = scalbnf(d1, -e);
+  d2 = scalbnf(d2, -e);
+  d3 = scalbnf(d3, -e);
+  if (d3 < 0.f) {
+    d1 = -d1;
+    d2 = -d2;
+    d3 = -d3;
+  }
+  return true;
+}
+
 // p - q scaled by a power of two so that max |d_k| is in [1, 2), signed so d3 >= 0.
 __device__ __forceinline__ bool circle_of(const float* __restrict__ P, const float* __restrict__ Q,
                                           int64_t i, float& d1, float& d2, float& d3) {
@@ -226,10 +257,19 @@ __device__ __forceinline__ bool circle_of(const float* __restrict__ P, const flo
   return true;
 }
 
+// Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
+constexpr int kSeg = 16;
+constexpr int kWalkers = 3;
+
+__device__ __forceinline__ int segments_of(uint32_t pk) {
+  const int l = (int)(pk >> 16) - (int)(pk & 0xffffu);
+  return l > 0 ? (l + kSeg - 1) / kSeg : 0;
+}
+
 // Per-warp circle table in shared memory, one column per lane (structure of arrays):
 // d1 d2 d3 inv3 jAB piece[0..7] offset, where offset is the circle's first segment in the
 // batch.
-constexpr int kRecWords = 14;
+constexpr int kRecWords = 18;  // 14 words of structure of arrays + 4 words of cumulative counts
 constexpr int kTabWords = kRecWords * 32;
 constexpr int kWalkThreads = 512;  // 16 warps: room for the tables beside the tile
 constexpr int kWalkWarps = kWalkThreads / 32;
@@ -243,16 +283,21 @@ __device__ __forceinline__ void store_rec(uint32_t* tab, int lane, const Prepare
 #pragma unroll
   for (int p = 0; p < 8; ++p) tab[(5 + p) * 32 + lane] = S.piece[p];
   tab[13 * 32 + lane] = (uint32_t)off;
+  // inclusive prefix counts of the pieces' segments, packed as u16 pairs (array of structures:
+  // one 16-byte record per circle)
+  uint32_t cum[4];
+  int acc = 0;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    acc += segments_of(S.piece[p]);
+    if (p & 1)
+      cum[p >> 1] |= (uint32_t)acc << 16;
+    else
+      cum[p >> 1] = (uint32_t)acc;
+  }
+  *reinterpret_cast<uint4*>(tab + 14 * 32 + 4 * lane) = make_uint4(cum[0], cum[1], cum[2], cum[3]);
 }
 
-// Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
-constexpr int kSeg = 16;
-constexpr int kWalkers = 3;
-
-__device__ __forceinline__ int segments_of(uint32_t pk) {
-  const int l = (int)(pk >> 16) - (int)(pk & 0xffffu);
-  return l > 0 ? (l + kSeg - 1) / kSeg : 0;
-}
 
 // One walker: a segment of one piece, advanced one major step per iteration. The cell is
 // tracked as a half-word index hb into the tile (two u16 counters per word, offset so that
@@ -297,20 +342,23 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   for (int s = 16; s > 0; s >>= 1)
     if ((int)tab[13 * 32 + k + s] <= sid) k += s;
   const int loc = sid - (int)tab[13 * 32 + k];
-  // the piece and the segment within it
-  int p = 0, seg = 0, lo = 0, plen = 0, acc = 0;
+  // the piece: the number of pieces whose inclusive segment count is <= loc; the segment
+  // within it: loc minus the largest such count
+  const uint4 cw = *reinterpret_cast<const uint4*>(tab + 14 * 32 + 4 * k);
+  const uint32_t cv[8] = {cw.x & 0xffffu, cw.x >> 16, cw.y & 0xffffu, cw.y >> 16,
+                          cw.z & 0xffffu, cw.z >> 16, cw.w & 0xffffu, cw.w >> 16};
+  int p = 0;
+  uint32_t before = 0;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const uint32_t pk = tab[(5 + q) * 32 + k];
-    const int nq = segments_of(pk);
-    if (nq > 0 && loc >= acc) {
-      p = q;
-      seg = loc - acc;
-      lo = (int)(pk & 0xffffu);
-      plen = (int)(pk >> 16) - lo;
-    }
-    acc += nq;
+    const bool done = cv[q] <= (uint32_t)loc;
+    p += done;
+    before = done ? cv[q] : before;
   }
+  const int seg = loc - (int)before;
+  const uint32_t pk = tab[(5 + p) * 32 + k];
+  const int lo = (int)(pk & 0xffffu);
+  const int plen = (int)(pk >> 16) - lo;
   const int c = lo + seg * kSeg;
   int len = min(kSeg, plen - seg * kSeg);
   const float d1 = __uint_as_float(tab[0 * 32 + k]), d2 = __uint_as_float(tab[1 * 32 + k]);
@@ -371,7 +419,8 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
 // is still beyond the following edge (a second crossing in the same step, which is rare).
 // A walker that leaves the grid never returns (each piece is monotone along its minor axis)
 // and its votes are masked by the window test, so the common step does not stop at the edge.
-__device__ __forceinline__ bool step_walker(Walker& w, bool act) {
+__device__ __forceinline__ bool step_walker(Walker& w, int i) {
+  const bool act = i < w.len;
   vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
   const bool mv = act && w.gx < -w.h;
   w.rel += mv ? w.dir : 0;
@@ -422,7 +471,7 @@ __device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, i
       bool more[kWalkers], any = false;
 #pragma unroll
       for (int j = 0; j < kWalkers; ++j) {
-        more[j] = step_walker(w[j], i < w[j].len);
+        more[j] = step_walker(w[j], i);
         any |= more[j];
       }
       if (__any_sync(kFull, any)) {
@@ -471,14 +520,21 @@ __global__ void __launch_bounds__(kWalkThreads, 1)
     const float* __restrict__ P = D.P;
     const float* __restrict__ Q = D.Q;
     const int64_t count = I.c1 - I.c0;
+    // the warp's batches of 32 circles; the next batch's pairs are loaded while this one is
+    // walked
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&s_next, 32);
+    base = __shfl_sync(kFull, base, 0);
+    float r[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (base + lane < count) load_pair(P, Q, I.c0 + base + lane, r);
     for (;;) {
-      int base = 0;
-      if (lane == 0) base = atomicAdd(&s_next, 32);
-      base = __shfl_sync(kFull, base, 0);
       if (base >= count) break;
       float e1 = 0.f, e2 = 0.f, e3 = 0.f;
-      bool live = false;
-      if (base + lane < count) live = circle_of(P, Q, I.c0 + base + lane, e1, e2, e3);
+      const bool live = base + lane < count && circle_from(r, e1, e2, e3);
+      int nbase = 0;
+      if (lane == 0) nbase = atomicAdd(&s_next, 32);
+      nbase = __shfl_sync(kFull, nbase, 0);
+      if (nbase + lane < count) load_pair(P, Q, I.c0 + nbase + lane, r);
       // phase A: this lane's circle
       Prepared S;
       int steps = 0;  // segments of this circle
@@ -500,11 +556,13 @@ __global__ void __launch_bounds__(kWalkThreads, 1)
 #pragma unroll
         for (int p = 0; p < 8; ++p) tab[(5 + p) * 32 + lane] = 0u;
         tab[13 * 32 + lane] = (uint32_t)(incl - steps);
+        *reinterpret_cast<uint4*>(tab + 14 * 32 + 4 * lane) = make_uint4(0u, 0u, 0u, 0u);
       }
       __syncwarp();
       // phase B: the whole batch
       if (total > 0) walk_batch(B, tab, total, lane);
       __syncwarp();
+      base = nbase;
     }
     __syncthreads();
 

@@ -85,9 +85,21 @@ def test_batch_small_instances_match_oracle(lib):
     for (pb, s), r, G in zip(inst, res, grids):
         want = oracle.solve(pb.P, pb.Q, G, 360, k=s["k"], nms_deg=2.0, tau=0.05)
         assert [x["cell"] for x in r] == [(row, col) for row, col, _ in want["peaks"]]
+        P64, Q64 = pb.P.astype(np.float64), pb.Q.astype(np.float64)
         for a, x in enumerate(r):
             assert x["bin"] == want["rotations"][a]["bin"]
-            assert parity.rot_diff(x["R"], want["rotations"][a]["R"]) < parity.E2E_ROT_TOL
+            sel = want["labels"] == a
+            assert x["n_inliers"] == int(sel.sum())
+            M = Q64[sel].T @ P64[sel]
+            sv = np.linalg.svd(M, compute_uv=False)
+            if sel.any() and sv[1] > 1e-6 * sv[0]:
+                assert parity.rot_diff(x["R"], want["rotations"][a]["R"]) < parity.E2E_ROT_TOL
+            else:
+                # one pair or collinear pairs: every maximiser of tr(R^T M) is correct
+                R = x["R"]
+                assert parity.rot_diff(R @ R.T, np.eye(3)) < 1e-12 and abs(np.linalg.det(R) - 1) < 1e-12
+                best = np.trace(want["rotations"][a]["R"].T @ M)
+                assert abs(np.trace(R.T @ M) - best) <= 1e-9 * max(1.0, sv[0])
 
 
 def test_server_results_equal_alone(lib):
