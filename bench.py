@@ -299,6 +299,10 @@ def run_sprot(args):
         out["cpu_baseline"] = cpu_baseline(prob, G, J, tau, args.cpu_sample)
         if not args.no_extras:
             try:
+                out["sampled_vote"] = run_sampled(B, P, Q, G)
+            except Exception as e:
+                out["sampled_vote"] = {"error": repr(e)}
+            try:
                 out["batched"] = run_batched(B, dev)
             except Exception as e:  # report, never hide
                 out["batched"] = {"error": repr(e)}
@@ -367,6 +371,28 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------
 # batched and served forms
 # ---------------------------------------------------------------------------------------
+
+def run_sampled(B, P, Q, G, J=360, reps=5):
+    """Algorithm 1's sampled accumulator (J points per circle) on the headline pairs."""
+    import torch
+
+    n = P.shape[0]
+    grid = torch.zeros(G * G, dtype=torch.int32, device=P.device)
+    B.axis_vote_sampled(P, Q, G, J, grid)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        B.axis_vote_sampled(P, Q, G, J, grid)
+    b.record(st)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    votes = int(grid.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+    return {"points_per_circle": J, "grid": G, "ms": ms, "Mcorr_per_s": n / ms / 1e3,
+            "Gpoints_per_s": n * J / ms / 1e6, "votes": votes, "Gvotes_per_s": votes / ms / 1e6,
+            "note": "L2 atomics (red.global.add) into the grid; inputs L2-warm"}
+
 
 def run_batched(B, dev, m=4096, loop_sample=512):
     """4096 uneven instances in one batched solve vs a per-instance loop of single solves."""

@@ -61,6 +61,7 @@ extern "C" {
 #define SPROT_MIN_GRID 16      /* G is a power of two in [16, 2048] */
 #define SPROT_MAX_GRID 2048
 #define SPROT_MAX_ANGLE_BINS 4096
+#define SPROT_MAX_SAMPLES 4096     /* points per circle of the sampled accumulator */
 
 /* Solver parameters. The paper fixes none of them; the defaults are those of
  * sprot_default_params(). */
@@ -149,6 +150,32 @@ int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n,
  * overwritten, not accumulated. Errors: E_INVAL (NULL, n < 1, bad G), E_NOMEM, E_CUDA. */
 int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size,
                     uint32_t* grid, void* stream);
+
+/* Least-squares rotation axis of a set of pairs (Eq. 10): the unit r minimising
+ * sum_i (z_i . r)^2 over the non-degenerate pairs with labels[i] == label (every pair when
+ * labels is NULL), z_i = (p_i - q_i)/|p_i - q_i| -- the eigenvector of S = sum_i z_i z_i^T for
+ * its smallest eigenvalue. S is summed in FP64 on the device (z_i in float32) and the
+ * eigenvector found by power iteration on adj(S). Used after the vote on its inliers, it
+ * refines the cell-resolution axis. P, Q, labels: device pointers. hint: host double[3] or
+ * NULL; r is signed so that r . hint >= 0, else r_z <= 0. axis: host double[3];
+ * lambda_min (the smallest eigenvalue, the residual sum of squares) and count (pairs used):
+ * host, may be NULL. Synchronous. Errors: E_INVAL, E_NOAXIS (fewer than two independent
+ * directions: the axis is not determined), E_NOMEM, E_CUDA. */
+int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* labels,
+                      int32_t label, const double* hint, double* axis, double* lambda_min,
+                      int64_t* count, void* stream);
+
+/* Algorithm 1's accumulator taken literally (its first loop): for every non-degenerate pair
+ * the great circle of z = (p - q)/|p - q| is drawn as J points alpha1 cos(t_j) +
+ * alpha2 sin(t_j), t_j = -pi + 2 pi j / J (the printed second cosine read as a sine), with
+ * alpha1 = the normalised component of alpha0 orthogonal to z (alpha0 = e3, or e1 when
+ * p - q has zero first and second components) and alpha2 = alpha1 x z. Each point is
+ * projected by Eq. 11 and, if inside the square [-1,1]^2, adds one to its cell of
+ * grid[G*G] (device uint32, row = v, col = u; overwritten, not accumulated). A circle can
+ * vote a cell several times and may miss a cell it only grazes. J <= SPROT_MAX_SAMPLES.
+ * Errors: E_INVAL (NULL, n < 1, bad G or J), E_CUDA. */
+int sprot_axis_vote_sampled(const float* P, const float* Q, int64_t n, int32_t grid_size,
+                            int32_t samples, uint32_t* grid, void* stream);
 
 /* Greedy top-k of a grid with non-maximum suppression (Sec. IV-D), on the device:
  * cells[2*i] = row, cells[2*i+1] = col, counts[i] = votes of peak i, for i < *n_found

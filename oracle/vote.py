@@ -363,6 +363,76 @@ def assign_labels(P, Q, R1s, tau: float):
     return labels, flag
 
 
+def eps_axis_vote(P, Q, G: int, eps: float):
+    """The consensus accumulator of Eq. 9 at cell resolution: circle i counts in cell c if
+    some axis r of the cell satisfies |r . z_i| < eps, z_i = d_i/|d_i|.
+
+    With F/(1 + u^2 + v^2) = d . r(u, v) (Eq. 12, 13), r . z < eps and r . z > -eps read
+    F_minus = F - eps |d| (1 + u^2 + v^2) < 0 and F_plus = F + eps |d| (1 + u^2 + v^2) > 0;
+    both are separable quadratics (circles of Eq. 13 with D != 0). The cell, being connected,
+    meets the band iff min_cell F_minus < 0 and max_cell F_plus > 0. eps = 0 leaves the open
+    version of the curve test; eps > 0 adds the cells within angular distance asin(eps) of the
+    great circle. The decision is flagged when either extreme is within BAND |d| of zero.
+    Returns dict(grid, lo, hi)."""
+    D, deg = _differences(P, Q)
+    e = grid_edges(G)
+    grid = np.zeros((G, G), dtype=np.int64)
+    lo = np.zeros((G, G), dtype=np.int64)
+    hi = np.zeros((G, G), dtype=np.int64)
+    for i in np.flatnonzero(~deg):
+        d = D[i]
+        nd = float(np.sqrt(d @ d))
+        cm, cp = d[2] - eps * nd, d[2] + eps * nd
+        # F_minus = cm (u^2 + v^2) + 2 d1 u + 2 d2 v - cp ; F_plus = cp (u^2 + v^2) + 2 d1 u + 2 d2 v - cm
+        gmin, _ = _quadratic_range(cm, 2.0 * d[0], e[:-1], e[1:])
+        hmin, _ = _quadratic_range(cm, 2.0 * d[1], e[:-1], e[1:])
+        _, gmax = _quadratic_range(cp, 2.0 * d[0], e[:-1], e[1:])
+        _, hmax = _quadratic_range(cp, 2.0 * d[1], e[:-1], e[1:])
+        Fm = hmin[:, None] + gmin[None, :] - cp
+        Fp = hmax[:, None] + gmax[None, :] - cm
+        voted = (Fm < 0.0) & (Fp > 0.0)
+        tol = BAND * nd
+        flag = (np.abs(Fm) <= tol) | (np.abs(Fp) <= tol)
+        grid += voted
+        lo += voted & ~flag
+        hi += voted | flag
+    return dict(grid=grid, lo=lo, hi=hi)
+
+
+def ls_axis(P, Q, select=None, hint=None):
+    """The least-squares rotation axis of a set of pairs (Eq. 10): the unit r minimising
+    sum_i (z_i . r)^2 with z_i = (p_i - q_i)/|p_i - q_i|, i.e. the eigenvector of
+    S = sum_i z_i z_i^T for its smallest eigenvalue (numpy eigh). ``select`` is a boolean
+    mask of the pairs to use (all when None); degenerate pairs are skipped. The sign is chosen
+    so that r . hint >= 0, or r_z <= 0 without a hint (ties: r_z < 0, then r_y < 0, ...).
+
+    Returns dict(axis, lam, S, gap) with lam the smallest eigenvalue (the residual sum of
+    squares) and gap = (second smallest - smallest) / largest eigenvalue, the conditioning of
+    the axis. axis is None when fewer than two independent directions are present."""
+    D, deg = _differences(P, Q)
+    use = ~deg if select is None else (np.asarray(select, dtype=bool) & ~deg)
+    Z = D[use]
+    if Z.shape[0] == 0:
+        return dict(axis=None, lam=0.0, S=np.zeros((3, 3)), gap=0.0)
+    Z = Z / np.linalg.norm(Z, axis=1, keepdims=True)
+    S = Z.T @ Z
+    w, V = np.linalg.eigh(S)
+    if w[1] <= 1e-12 * max(w[2], 1e-300):
+        return dict(axis=None, lam=float(w[0]), S=S, gap=0.0)
+    r = V[:, 0]
+    ref = np.asarray(hint, dtype=np.float64) if hint is not None else None
+    if ref is not None:
+        if r @ ref < 0:
+            r = -r
+    else:
+        for k in (2, 1, 0):
+            if r[k] != 0.0:
+                if r[k] > 0:
+                    r = -r
+                break
+    return dict(axis=r, lam=float(w[0]), S=S, gap=float((w[1] - w[0]) / w[2]))
+
+
 # ---------------------------------------------------------------------------------------
 # Algorithm 1's sampled rasteriser (used as a pin of the cell predicate)
 # ---------------------------------------------------------------------------------------
@@ -391,6 +461,76 @@ def sampled_circle_cells(d, G: int, J: int, alpha0=(0.0, 0.0, 1.0)):
     cols = np.floor((uv[:, 0] + 1.0) * G / 2.0).astype(int)
     rows = np.floor((uv[:, 1] + 1.0) * G / 2.0).astype(int)
     return set(zip(rows.tolist(), cols.tolist()))
+
+
+#: half-width (plane units, times 1 + 1/|alpha0 - (alpha0.z) z|) of the band around cell edges
+#: inside which a float32 sample may fall on either side
+SAMPLE_BAND = 1e-5
+
+
+def sample_basis(d):
+    """The basis of the great circle of d used by Algorithm 1: z = d/|d|; alpha0 = e3 unless
+    d1 = d2 = 0 exactly (then z = +-e3 and alpha0 = e1); alpha1 = alpha0 - (alpha0 . z) z
+    (the projection of Algorithm 1 removed) normalised; alpha2 = alpha1 x z.
+    Returns (alpha1, alpha2, |alpha0 - (alpha0 . z) z|).
+
+    Reading: Algorithm 1 leaves alpha0 open; the rule above is one whose branch is decided
+    exactly in any precision (d1 = d2 = 0 is a test on the inputs)."""
+    d = np.asarray(d, dtype=np.float64)
+    z = d / np.linalg.norm(d)
+    a0 = np.array([1.0, 0.0, 0.0]) if (d[0] == 0.0 and d[1] == 0.0) else np.array([0.0, 0.0, 1.0])
+    a1 = a0 - (a0 @ z) * z
+    na = float(np.linalg.norm(a1))
+    a1 = a1 / na
+    return a1, np.cross(a1, z), na
+
+
+def sampled_axis_vote(P, Q, G: int, J: int):
+    """Algorithm 1's accumulator taken literally: for every pair, the J points
+    alpha1 cos(t_j) + alpha2 sin(t_j) of its great circle, t_j = -pi + 2 pi j / J, are
+    projected by Eq. 11 and each point inside the square adds one to its cell. A circle can
+    therefore vote a cell several times, and a cell it only grazes may get no vote. (The
+    printed second cosine is read as a sine.) Degenerate pairs (d = 0) do not vote.
+
+    Flags: a sample whose u or v lies within eta = SAMPLE_BAND (1 + 1/|alpha0 - (alpha0.z)z|)
+    of a cell edge (or of the square's border) may land on either side in float32; it counts
+    in ``hi`` for every candidate cell and not in ``lo``.
+    Returns dict(grid, lo, hi) of int64 G x G arrays [row (v), col (u)]."""
+    D, deg = _differences(P, Q)
+    t = -math.pi + 2.0 * math.pi * np.arange(J) / J
+    ct, st = np.cos(t), np.sin(t)
+    grid = np.zeros((G, G), dtype=np.int64)
+    lo = np.zeros((G, G), dtype=np.int64)
+    hi = np.zeros((G, G), dtype=np.int64)
+    half = G / 2.0
+    for i in np.flatnonzero(~deg):
+        a1, a2, na = sample_basis(D[i])
+        pts = ct[:, None] * a1[None, :] + st[:, None] * a2[None, :]
+        w = 1.0 - pts[:, 2]
+        ok = w > 0.0
+        u = np.where(ok, pts[:, 0] / np.where(ok, w, 1.0), np.inf)
+        v = np.where(ok, pts[:, 1] / np.where(ok, w, 1.0), np.inf)
+        eta = SAMPLE_BAND * (1.0 + 1.0 / na) * half  # in cell units
+        fu, fv = (u + 1.0) * half, (v + 1.0) * half
+        inside = (np.abs(u) < 1.0) & (np.abs(v) < 1.0)
+        with np.errstate(invalid="ignore"):  # points at the pole: inf - inf, never flagged
+            near_u = np.abs(fu - np.round(fu)) <= eta
+            near_v = np.abs(fv - np.round(fv)) <= eta
+        flag = (near_u | near_v) & np.isfinite(fu) & np.isfinite(fv)
+        col = np.floor(fu[inside]).astype(np.int64)
+        row = np.floor(fv[inside]).astype(np.int64)
+        np.add.at(grid, (row, col), 1)
+        sure = inside & ~flag
+        np.add.at(lo, (np.floor(fv[sure]).astype(np.int64), np.floor(fu[sure]).astype(np.int64)), 1)
+        np.add.at(hi, (np.floor(fv[sure]).astype(np.int64), np.floor(fu[sure]).astype(np.int64)), 1)
+        for k in np.flatnonzero(flag):
+            cols = {int(np.floor(fu[k] - eta)), int(np.floor(fu[k] + eta))}
+            rows = {int(np.floor(fv[k] - eta)), int(np.floor(fv[k] + eta))}
+            for r in rows:
+                for c in cols:
+                    if 0 <= r < G and 0 <= c < G:
+                        hi[r, c] += 1
+    return dict(grid=grid, lo=lo, hi=hi)
 
 
 # ---------------------------------------------------------------------------------------

@@ -22,6 +22,7 @@ MAX_K = 8
 EXPORTS = [
     "sprot_default_params", "sprot_status_string", "sprot_estimate_rotation",
     "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex", "sprot_axis_vote",
+    "sprot_axis_vote_sampled", "sprot_refine_axis",
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
@@ -105,6 +106,9 @@ def load(path: str = LIB_PATH):
     lib.sprot_estimate_rotations_ex.argtypes = [vp, vp, i64, C.POINTER(Params), C.POINTER(Rotation),
                                                 C.POINTER(i32), vp, C.POINTER(Debug), vp]
     lib.sprot_axis_vote.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.sprot_axis_vote_sampled.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+    lib.sprot_refine_axis.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(i64), vp]
     lib.sprot_select_peaks.argtypes = [vp, i32, i32, C.c_float, vp, vp, vp, vp]
     lib.sprot_estimate_batch.argtypes = [C.POINTER(Instance), i64, vp]
     lib.sprot_autotune_grid.argtypes = [i64]
@@ -123,7 +127,8 @@ def load(path: str = LIB_PATH):
     lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
     lib.sprot_kernel_timing_read.restype = None
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
-                 "sprot_axis_vote", "sprot_select_peaks", "sprot_estimate_batch",
+                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_refine_axis", "sprot_select_peaks",
+                 "sprot_estimate_batch",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
                  "sprot_server_destroy", "sprot_probe_smem_atomic_rate"]:
         getattr(lib, name).restype = C.c_int
@@ -212,6 +217,31 @@ def axis_vote(P, Q, G: int, grid, stream=None):
     _check_points(P, Q)
     st = load().sprot_axis_vote(_ptr(P), _ptr(Q), P.shape[0], int(G), _ptr(grid), _stream(stream))
     check(st, "sprot_axis_vote")
+
+
+def axis_vote_sampled(P, Q, G: int, J: int, grid, stream=None):
+    """Fills the device tensor ``grid`` (G*G 32-bit) with Algorithm 1's sampled accumulator
+    (J points per circle)."""
+    _check_points(P, Q)
+    st = load().sprot_axis_vote_sampled(_ptr(P), _ptr(Q), P.shape[0], int(G), int(J), _ptr(grid),
+                                        _stream(stream))
+    check(st, "sprot_axis_vote_sampled")
+
+
+def refine_axis(P, Q, labels=None, label: int = 0, hint=None, stream=None):
+    """Least-squares axis (Eq. 10) of the pairs with labels == label (all pairs when labels
+    is None). Returns dict(axis, lambda_min, count) or None when the axis is not determined."""
+    _check_points(P, Q)
+    axis = (C.c_double * 3)()
+    lam = C.c_double(0.0)
+    cnt = C.c_int64(0)
+    h = (C.c_double * 3)(*[float(x) for x in hint]) if hint is not None else None
+    st = load().sprot_refine_axis(_ptr(P), _ptr(Q), P.shape[0], _ptr(labels), int(label), h, axis,
+                                  C.byref(lam), C.byref(cnt), _stream(stream))
+    if st == E_NOAXIS:
+        return None
+    check(st, "sprot_refine_axis")
+    return dict(axis=np.array(axis[:]), lambda_min=lam.value, count=cnt.value)
 
 
 def select_peaks(grid, G: int, k: int, nms_deg: float, cells, counts, n_found, stream=None):

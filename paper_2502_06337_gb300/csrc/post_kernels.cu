@@ -752,12 +752,13 @@ __device__ bool polar_start_f32(const double* Xd, double* q) {
 // 1 + 1e-7 cond to the quadratic convergence. q is left unnormalised until the end (a scale
 // of U scales v and H alike and leaves w unchanged). From a float32 start three steps reach
 // the FP64 rounding floor. Returns false if the system is not positive definite or the last
-// correction is not below 5e-12 (the iteration did not settle).
+// correction is not below 5e-12 (the iteration did not settle). The loop ends once a correction
+// is below 1e-12: the error left is then of the order of its square.
 __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
   float Xf[9];
   for (int t = 0; t < 9; ++t) Xf[t] = (float)X[t];
   float n2 = 1.f;
-  for (int it = 0; it < 4 && n2 >= 1e-30f; ++it) {
+  for (int it = 0; it < 4 && n2 >= 1e-24f; ++it) {
     quat_to_rot(q, R);  // |q|^2 times a rotation
     // v in FP64
     const double v0 = (R[2] * X[1] + R[5] * X[4] + R[8] * X[7]) - (R[1] * X[2] + R[4] * X[5] + R[7] * X[8]);
@@ -795,36 +796,46 @@ __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
   return n2 < 2.5e-23f;
 }
 
+constexpr int kKabschThreads = 320;  // ten warps: one per summed quantity in the second stage
+
 // phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One block per
-// (instance, rotation): the item partials are summed in a fixed order (thread t takes items
-// t, t + 256, ...; then warps, then the block), and thread 0 solves for the rotation.
-__global__ void __launch_bounds__(256) k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
+// (instance, rotation). The item partials are summed in a fixed order: thread t adds items
+// t, t + 320, ...; then warp j adds quantity j over the 320 threads. A dependent FP64
+// operation costs tens of cycles on this part, so the chains are kept short: the singularity
+// test needs no square root and X is M scaled by a power of two (the polar factor does not
+// depend on the scale).
+__global__ void __launch_bounds__(kKabschThreads) k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
   const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
   const InstDev& D = insts[inst];
   if (a >= *D.n_found) return;
-  double s[10];
+  __shared__ double part[kKabschThreads][10];
+  __shared__ double tot[10];
+  {
+    double v[10];
 #pragma unroll
-  for (int t = 0; t < 10; ++t) s[t] = 0.0;
-  const double* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
-  for (int it = threadIdx.x; it < D.n_items; it += blockDim.x) {
-    const double* src = base + (int64_t)it * D.k * 10;
+    for (int t = 0; t < 10; ++t) v[t] = 0.0;
+    const double* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
+    for (int it = threadIdx.x; it < D.n_items; it += blockDim.x) {
+      const double* src = base + (int64_t)it * D.k * 10;
 #pragma unroll
-    for (int t = 0; t < 10; ++t) s[t] += src[t];
+      for (int t = 0; t < 10; ++t) v[t] += src[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 10; ++t) part[threadIdx.x][t] = v[t];
   }
-  __shared__ double red[8][10];
+  __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int t = 0; t < 10; ++t) {
-    const double v = warp_sum_d(s[t]);
-    if (l == 0) red[w][t] = v;
+  if (w < 10) {
+    double v = 0.0;
+    for (int i = l; i < kKabschThreads; i += 32) v += part[i][w];
+    v = warp_sum_d(v);
+    if (l == 0) tot[w] = v;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  for (int t = 0; t < 10; ++t) {
-    double v = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i][t];
-    s[t] = v;
-  }
+  double s[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) s[t] = tot[t];
   DevRot& R = D.rot[a];
   double out[9];
   const uint32_t cnt = (uint32_t)s[9];
@@ -832,16 +843,21 @@ __global__ void __launch_bounds__(256) k_kabsch(const InstDev* __restrict__ inst
     const double* fb = phase == 0 ? R.R_vote : R.R_init;
     for (int t = 0; t < 9; ++t) out[t] = fb[t];
   } else {
-    // M / |M|_F has the same polar factor; det > 0 (beyond rounding) selects the polar path
-    double n2 = 0.0;
-    for (int t = 0; t < 9; ++t) n2 += s[t] * s[t];
+    // det M > 1e-9 |M|_F^3 (polar path) tested as det > 0 and det^2 > 1e-18 (|M|_F^2)^3
+    const double c0 = s[4] * s[8] - s[5] * s[7], c1 = s[5] * s[6] - s[3] * s[8], c2 = s[3] * s[7] - s[4] * s[6];
+    const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
+    const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
+                      (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
+    // X = M 2^-e with the largest |entry| in [1, 2) (exact)
+    double mx = 0.0;
+    for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
+    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
     double X[9];
-    const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-    for (int t = 0; t < 9; ++t) X[t] = s[t] * inv;
-    const double det = X[0] * (X[4] * X[8] - X[5] * X[7]) - X[1] * (X[3] * X[8] - X[5] * X[6]) +
-                       X[2] * (X[3] * X[7] - X[4] * X[6]);
+    for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
     double q[4];
-    const bool ok = det > 1e-9 && polar_start_f32(X, q) && polar_refine_f64(X, q, out);
+    const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
+                    polar_start_f32(X, q) && polar_refine_f64(X, q, out);
     if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
   }
   if (phase == 0) {
@@ -855,6 +871,166 @@ __global__ void __launch_bounds__(256) k_kabsch(const InstDev* __restrict__ inst
     R.n_inliers = cnt;
     R.n_degenerate = *D.n_deg;
   }
+}
+
+// ---- least-squares axis of a set of pairs (Eq. 10) ---------------------------------------
+
+constexpr int kAxisThreads = 256;
+
+// S = sum z z^T (6 distinct entries, FP64) over the selected non-degenerate pairs of one chunk,
+// z = (p - q)/|p - q| in float32 (its products are exact in FP64). Pairs are queued per warp
+// and summed over full warps only, as in the rotation sums. partial[block] = 6 sums + count.
+__global__ void __launch_bounds__(kAxisThreads)
+    k_axis_sums(const float* __restrict__ P, const float* __restrict__ Q, int64_t n,
+                const int32_t* __restrict__ labels, int label, int chunk, double* __restrict__ partial) {
+  __shared__ int queue[kAxisThreads / 32][64];
+  __shared__ double red[kAxisThreads / 32][7];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = n < i0 + chunk ? n : i0 + chunk;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int len = 0, total = 0;
+  auto add = [&](int64_t i) {
+    float d1 = __ldg(P + 3 * i) - __ldg(Q + 3 * i);
+    float d2 = __ldg(P + 3 * i + 1) - __ldg(Q + 3 * i + 1);
+    float d3 = __ldg(P + 3 * i + 2) - __ldg(Q + 3 * i + 2);
+    const int e = ilogbf(fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3))));
+    d1 = scalbnf(d1, -e);
+    d2 = scalbnf(d2, -e);
+    d3 = scalbnf(d3, -e);
+    const float r = rsqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
+    const double z1 = d1 * r, z2 = d2 * r, z3 = d3 * r;
+    acc[0] = fma(z1, z1, acc[0]);
+    acc[1] = fma(z1, z2, acc[1]);
+    acc[2] = fma(z1, z3, acc[2]);
+    acc[3] = fma(z2, z2, acc[3]);
+    acc[4] = fma(z2, z3, acc[4]);
+    acc[5] = fma(z3, z3, acc[5]);
+  };
+  for (int64_t base = i0 + 32 * wp; base < i1; base += blockDim.x) {
+    const int64_t i = base + lane;
+    bool sel = false;
+    if (i < i1 && (!labels || labels[i] == label)) {
+      sel = __ldg(P + 3 * i) != __ldg(Q + 3 * i) || __ldg(P + 3 * i + 1) != __ldg(Q + 3 * i + 1) ||
+            __ldg(P + 3 * i + 2) != __ldg(Q + 3 * i + 2);
+    }
+    const unsigned bal = __ballot_sync(kFull, sel);
+    if (!bal) continue;
+    const int pos = len + __popc(bal & ((1u << lane) - 1u));
+    if (sel) queue[wp][pos] = (int)(i - i0);
+    len += __popc(bal);
+    total += __popc(bal);
+    if (len >= 32) {
+      __syncwarp();
+      add(i0 + queue[wp][lane]);
+      const int rest = len - 32;
+      const int moved = lane < rest ? queue[wp][32 + lane] : 0;
+      __syncwarp();
+      if (lane < rest) queue[wp][lane] = moved;
+      __syncwarp();
+      len = rest;
+    }
+  }
+  __syncwarp();
+  if (lane < len) add(i0 + queue[wp][lane]);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double v = warp_sum_d(acc[t]);
+    if (lane == 0) red[wp][t] = v;
+  }
+  if (lane == 0) red[wp][6] = (double)total;
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0.0;
+    for (int w = 0; w < kAxisThreads / 32; ++w) v += red[w][threadIdx.x];
+    partial[(int64_t)blockIdx.x * 8 + threadIdx.x] = v;
+  }
+}
+
+// Sum of the partials (fixed order) and the eigenvector of S for its smallest eigenvalue by
+// power iteration on adj(S): adj(S) has the eigenvalues lambda_j lambda_k (pairs of S's), the
+// largest belonging to S's smallest eigenvector, and converges at the rate lambda_min /
+// lambda_mid from its largest column. out = axis[3], lambda_min, count, status.
+__global__ void __launch_bounds__(kAxisThreads)
+    k_axis_eig(const double* __restrict__ partial, int nb, double h0, double h1, double h2, int has_hint,
+               double* __restrict__ out) {
+  __shared__ double part[kAxisThreads][7];
+  __shared__ double tot[7];
+  {
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+      for (int t = 0; t < 7; ++t) v[t] += partial[(int64_t)b * 8 + t];
+#pragma unroll
+    for (int t = 0; t < 7; ++t) part[threadIdx.x][t] = v[t];
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < 7) {
+    double v = 0.0;
+    for (int i = l; i < kAxisThreads; i += 32) v += part[i][w];
+    v = warp_sum_d(v);
+    if (l == 0) tot[w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double s00 = tot[0], s01 = tot[1], s02 = tot[2], s11 = tot[3], s12 = tot[4], s22 = tot[5];
+  out[4] = tot[6];
+  const double A[9] = {s11 * s22 - s12 * s12, s02 * s12 - s01 * s22, s01 * s12 - s02 * s11,
+                       s02 * s12 - s01 * s22, s00 * s22 - s02 * s02, s01 * s02 - s00 * s12,
+                       s01 * s12 - s02 * s11, s01 * s02 - s00 * s12, s00 * s11 - s01 * s01};
+  double best = -1.0, x[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) {
+    const double nk = A[k] * A[k] + A[3 + k] * A[3 + k] + A[6 + k] * A[6 + k];
+    if (nk > best) {
+      best = nk;
+      x[0] = A[k];
+      x[1] = A[3 + k];
+      x[2] = A[6 + k];
+    }
+  }
+  const double tr = s00 + s11 + s22;
+  // fewer than two independent directions: adj(S) vanishes (relative to trace(S)^2)
+  if (!(best > 1e-24 * (tr * tr) * (tr * tr))) {
+    out[5] = (double)SPROT_E_NOAXIS;
+    return;
+  }
+  for (int it = 0; it < 64; ++it) {
+    // exact power-of-two rescaling keeps x in range
+    const double mx = fmax(fabs(x[0]), fmax(fabs(x[1]), fabs(x[2])));
+    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+    const double y0 = x[0] * sc, y1 = x[1] * sc, y2 = x[2] * sc;
+    const double n0 = A[0] * y0 + A[1] * y1 + A[2] * y2;
+    const double n1 = A[3] * y0 + A[4] * y1 + A[5] * y2;
+    const double n2 = A[6] * y0 + A[7] * y1 + A[8] * y2;
+    // change of direction: |x_new/|x_new| - x_old/|x_old||^2 via the cosine
+    const double nn = n0 * n0 + n1 * n1 + n2 * n2, yy = y0 * y0 + y1 * y1 + y2 * y2;
+    const double dot = n0 * y0 + n1 * y1 + n2 * y2;
+    x[0] = n0;
+    x[1] = n1;
+    x[2] = n2;
+    if (dot > 0.0 && 1.0 - dot * dot / (nn * yy) < 1e-30) break;
+  }
+  const double rn = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  double r0 = x[0] * rn, r1 = x[1] * rn, r2 = x[2] * rn;
+  bool flip;
+  if (has_hint) {
+    flip = r0 * h0 + r1 * h1 + r2 * h2 < 0.0;
+  } else {  // r_z <= 0 (then r_y, r_x for ties at zero)
+    flip = r2 != 0.0 ? r2 > 0.0 : (r1 != 0.0 ? r1 > 0.0 : r0 > 0.0);
+  }
+  if (flip) {
+    r0 = -r0;
+    r1 = -r1;
+    r2 = -r2;
+  }
+  out[0] = r0;
+  out[1] = r1;
+  out[2] = r2;
+  // Rayleigh quotient: the smallest eigenvalue
+  out[3] = r0 * (s00 * r0 + s01 * r1 + s02 * r2) + r1 * (s01 * r0 + s11 * r1 + s12 * r2) +
+           r2 * (s02 * r0 + s12 * r1 + s22 * r2);
+  out[5] = (double)SPROT_OK;
 }
 
 // Peaks of a caller grid as (row, col) pairs and counts (stage entry point).
@@ -930,7 +1106,7 @@ void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* in
 }
 
 void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st) {
-  k_kabsch<<<m * max_k, 256, 0, st>>>(insts, max_k, phase);
+  k_kabsch<<<m * max_k, kKabschThreads, 0, st>>>(insts, max_k, phase);
   launches_add(1);
 }
 
@@ -945,6 +1121,14 @@ void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts
   else
     k_label_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
   launches_add(1);
+}
+
+void launch_axis_ls(const float* P, const float* Q, int64_t n, const int32_t* labels, int label, int chunk,
+                    int nb, double* partial, const double* hint, double* out, cudaStream_t st) {
+  k_axis_sums<<<nb, kAxisThreads, 0, st>>>(P, Q, n, labels, label, chunk, partial);
+  k_axis_eig<<<1, kAxisThreads, 0, st>>>(partial, nb, hint ? hint[0] : 0.0, hint ? hint[1] : 0.0,
+                                         hint ? hint[2] : 0.0, hint ? 1 : 0, out);
+  launches_add(2);
 }
 
 }  // namespace sprot

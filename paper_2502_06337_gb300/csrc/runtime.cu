@@ -636,6 +636,45 @@ int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t G, uint32
   return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* labels, int32_t label,
+                      const double* hint, double* axis, double* lambda_min, int64_t* count, void* stream) {
+  if (!P || !Q || !axis || n < 1 || n > (int64_t)1 << 31) return SPROT_E_INVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int status = SPROT_OK;
+  Workspace* ws = workspace_for(st, &status);
+  if (!ws) return status;
+  std::lock_guard<std::mutex> lock(ws->mu);
+  const int chunk = kStreamChunk;
+  const int nb = (int)((n + chunk - 1) / chunk);
+  const size_t part_bytes = align_up(sizeof(double) * 8 * (size_t)nb);
+  status = ws->reserve(part_bytes + align_up(sizeof(double) * 8), align_up(sizeof(double) * 8));
+  if (status != SPROT_OK) return status;
+  double* dpart = reinterpret_cast<double*>(ws->dev);
+  double* dout = reinterpret_cast<double*>(ws->dev + part_bytes);
+  double* hout = reinterpret_cast<double*>(ws->host);
+  launch_axis_ls(P, Q, n, labels, label, chunk, nb, dpart, hint, dout, st);
+  if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
+  if (cudaMemcpyAsync(hout, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SPROT_E_CUDA;
+  if (count) *count = (int64_t)hout[4];
+  const int res = (int)hout[5];
+  if (res != SPROT_OK) return res;
+  for (int t = 0; t < 3; ++t) axis[t] = hout[t];
+  if (lambda_min) *lambda_min = hout[3];
+  return SPROT_OK;
+}
+
+int sprot_axis_vote_sampled(const float* P, const float* Q, int64_t n, int32_t G, int32_t J,
+                            uint32_t* grid, void* stream) {
+  if (!P || !Q || !grid || n < 1 || n > (int64_t)1 << 31 || !is_pow2(G) || G < SPROT_MIN_GRID ||
+      G > SPROT_MAX_GRID || J < 1 || J > SPROT_MAX_SAMPLES)
+    return SPROT_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPROT_E_CUDA;
+  return launch_axis_vote_sampled(P, Q, n, G, J, grid, sm_count(dev), reinterpret_cast<cudaStream_t>(stream));
+}
+
 int sprot_select_peaks(const uint32_t* grid, int32_t G, int32_t k, float nms_deg, int32_t* cells,
                        uint32_t* counts, int32_t* n_found, void* stream) {
   if (!grid || !cells || !counts || !n_found || !is_pow2(G) || G < SPROT_MIN_GRID ||

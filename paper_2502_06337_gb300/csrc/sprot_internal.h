@@ -98,6 +98,15 @@ size_t problem_footprint(int64_t n, int G, int J, int k);
 // Axis vote (vote_walk.cu). tile_bytes: the largest band tile of the launch; the kernel adds
 // its per-warp circle tables (vote_table_bytes()) to the dynamic shared memory.
 int vote_table_bytes();
+// Least-squares axis (post_kernels.cu): FP64 sums of z z^T over the selected pairs in nb chunks
+// of `chunk` pairs into partial[nb][8], then out[6] = axis[3], lambda_min, count, status.
+// hint: host double[3] or NULL.
+void launch_axis_ls(const float* P, const float* Q, int64_t n, const int32_t* labels, int label, int chunk,
+                    int nb, double* partial, const double* hint, double* out, cudaStream_t st);
+// Algorithm 1's sampled accumulator (vote_sampled.cu): zeroes grid[G*G] and adds one per drawn
+// point of every circle, J points per circle.
+int launch_axis_vote_sampled(const float* P, const float* Q, int64_t n, int G, int J, uint32_t* grid,
+                             int n_sm, cudaStream_t st);
 void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
                            int grid_ctas, int tile_bytes, cudaStream_t st);
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,

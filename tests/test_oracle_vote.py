@@ -358,3 +358,167 @@ def test_cap_between_corners_is_voted(swap):
     assert Fmin[row, col] < -1e-3 and Fmax[row, col] > 0
     av = oracle.axis_vote(np.asarray([d], np.float32), np.zeros((1, 3), np.float32), G)
     assert av["grid"][row, col] == 1 and av["lo"][row, col] == 1
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 1's sampled accumulator (the literal J-point rasteriser)
+# ---------------------------------------------------------------------------------------
+
+def test_sample_basis_spans_the_great_circle():
+    rng = np.random.default_rng(40)
+    for d in list(rng.standard_normal((20, 3))) + [np.array([0.0, 0.0, 2.5]), np.array([0.0, 0.0, -1.0])]:
+        a1, a2, na = ov.sample_basis(d)
+        z = d / np.linalg.norm(d)
+        for v in (a1, a2):
+            assert abs(np.linalg.norm(v) - 1.0) < 1e-14 and abs(v @ z) < 1e-14
+        assert abs(a1 @ a2) < 1e-14 and na > 0
+
+
+def test_sampled_unit_circle_closed_form():
+    """z = e3 (the equator, i.e. the unit circle of the plane): alpha0 = e1, alpha1 = e1,
+    alpha2 = e1 x e3 = -e2, so sample j is (cos t_j, -sin t_j) in the plane; each cell's count
+    is the number of angles whose point lies in it (several per cell: double votes)."""
+    P = np.array([[0.3, -0.2, 1.5]], dtype=np.float32)
+    Q = np.array([[0.3, -0.2, 0.5]], dtype=np.float32)  # d = (0, 0, 1)
+    for G, J in ((4, 7), (8, 90), (2, 720)):
+        got = ov.sampled_axis_vote(P, Q, G, J)
+        want = np.zeros((G, G), dtype=np.int64)
+        for j in range(J):
+            t = -math.pi + 2.0 * math.pi * j / J
+            u, v = math.cos(t), -math.sin(t)
+            if abs(u) < 1.0 and abs(v) < 1.0:
+                want[int(math.floor((v + 1.0) * G / 2)), int(math.floor((u + 1.0) * G / 2))] += 1
+        assert np.array_equal(got["grid"], want)
+        assert want.max() > 1 or J < G * 4  # several samples share a cell
+
+
+def test_sampled_cells_lie_on_the_predicate_cells():
+    """Every sample that is not near an edge lands in a cell the closed-cell test votes."""
+    prob = synth.make_problem(40, (0.5,), 0.01, seed=41)
+    G = 32
+    for i in range(prob.n):
+        P1, Q1 = prob.P[i:i + 1], prob.Q[i:i + 1]
+        sv = ov.sampled_axis_vote(P1, Q1, G, 500)
+        av = oracle.axis_vote(P1, Q1, G)
+        assert np.all((sv["lo"] == 0) | (av["hi"] > 0))
+
+
+def test_sampled_swap_invariance():
+    """Swapping P and Q negates z: alpha1 is unchanged, alpha2 flips, and the angle set
+    {t_j} is symmetric under t -> -t, so the same points are drawn."""
+    prob = synth.make_problem(60, (0.4,), 0.01, seed=42)
+    a = ov.sampled_axis_vote(prob.P, prob.Q, 64, 180)
+    b = ov.sampled_axis_vote(prob.Q, prob.P, 64, 180)
+    assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"])
+
+
+# ---------------------------------------------------------------------------------------
+# Least-squares axis (Eq. 10)
+# ---------------------------------------------------------------------------------------
+
+def test_ls_axis_noise_free_is_the_rotation_axis():
+    """Every noise-free inlier has z . r = 0 for the true axis r (Eq. 8), so the smallest
+    eigenvalue of S is 0 and its eigenvector is r (up to sign)."""
+    rng = np.random.default_rng(60)
+    for _ in range(5):
+        prob = synth.make_problem(400, (1.0,), 0.0, seed=int(rng.integers(1 << 30)))
+        R = prob.rotations[0]
+        w, V = np.linalg.eig(R)
+        r_true = np.real(V[:, np.argmin(np.abs(w - 1.0))])
+        got = ov.ls_axis(prob.P, prob.Q, hint=r_true)
+        assert got["lam"] < 1e-9
+        assert np.linalg.norm(got["axis"] - r_true / np.linalg.norm(r_true)) < 1e-6
+
+
+def test_ls_axis_matches_singular_vector_of_stacked_constraints():
+    """The same axis from the stacked system of Eq. 10 by SVD (right singular vector of the
+    smallest singular value), with outliers and noise."""
+    prob = synth.make_problem(500, (0.6,), 0.02, seed=61)
+    sel = prob.truth == 0
+    got = ov.ls_axis(prob.P, prob.Q, sel)
+    D = prob.P[sel].astype(np.float64) - prob.Q[sel].astype(np.float64)
+    Z = D / np.linalg.norm(D, axis=1, keepdims=True)
+    _, sv, Vt = np.linalg.svd(Z)
+    r = Vt[-1]
+    r = r if r @ got["axis"] >= 0 else -r
+    assert np.linalg.norm(r - got["axis"]) < 1e-9
+    assert abs(sv[-1] ** 2 - got["lam"]) < 1e-9 * sv[0] ** 2
+
+
+def test_ls_axis_is_equivariant_and_needs_two_directions():
+    prob = synth.make_problem(300, (1.0,), 0.01, seed=62)
+    S = synth.random_rotation(np.random.default_rng(63))
+    a = ov.ls_axis(prob.P, prob.Q)
+    b = ov.ls_axis((prob.P.astype(np.float64) @ S.T), (prob.Q.astype(np.float64) @ S.T), hint=S @ a["axis"])
+    assert np.linalg.norm(b["axis"] - S @ a["axis"]) < 1e-9
+    one = ov.ls_axis(prob.P[:1], prob.Q[:1])
+    assert one["axis"] is None
+
+
+# ---------------------------------------------------------------------------------------
+# The eps-band consensus accumulator (Eq. 9)
+# ---------------------------------------------------------------------------------------
+
+def _annulus_cells(G, eps):
+    """z = e3: |r . z| = |r_z| = |s - 1| / (s + 1) with s = u^2 + v^2 (Eq. 12), so the band is
+    the open annulus (1 - eps)/(1 + eps) < s < (1 + eps)/(1 - eps); a closed cell meets it iff
+    its nearest point to the origin is inside the outer circle and its farthest outside the
+    inner one."""
+    e = -1.0 + 2.0 * np.arange(G + 1) / G
+    s_in, s_out = (1 - eps) / (1 + eps), (1 + eps) / (1 - eps)
+    want = np.zeros((G, G), dtype=np.int64)
+    for r in range(G):
+        for c in range(G):
+            u0, u1, v0, v1 = e[c], e[c + 1], e[r], e[r + 1]
+            nu = 0.0 if u0 <= 0 <= u1 else min(abs(u0), abs(u1))
+            nv = 0.0 if v0 <= 0 <= v1 else min(abs(v0), abs(v1))
+            fu, fv = max(abs(u0), abs(u1)), max(abs(v0), abs(v1))
+            want[r, c] = (nu * nu + nv * nv < s_out) and (fu * fu + fv * fv > s_in)
+    return want
+
+
+def test_eps_band_unit_circle_is_an_annulus():
+    P = np.array([[0.2, 0.1, 0.9]], dtype=np.float32)
+    Q = np.array([[0.2, 0.1, 0.4]], dtype=np.float32)  # d = (0, 0, 0.5)
+    for G, eps in ((16, 0.05), (32, 0.2), (64, 0.01)):
+        got = ov.eps_axis_vote(P, Q, G, eps)
+        want = _annulus_cells(G, eps)
+        certain = got["lo"] == got["hi"]
+        assert np.array_equal(got["grid"][certain], want[certain]) and certain.mean() > 0.99
+
+
+def test_eps_band_contains_sampled_band_points():
+    """Dense points of each cell with |r . z| < eps (r by Eq. 12) lie only in voted cells,
+    and the band grows with eps."""
+    prob = synth.make_problem(6, (0.5,), 0.01, seed=70)
+    G = 16
+    m = 12
+    t = (np.arange(m) + 0.5) / m
+    for eps in (0.02, 0.1):
+        for i in range(prob.n):
+            P1, Q1 = prob.P[i:i + 1], prob.Q[i:i + 1]
+            got = ov.eps_axis_vote(P1, Q1, G, eps)
+            d = P1[0].astype(np.float64) - Q1[0]
+            z = d / np.linalg.norm(d)
+            for r in range(G):
+                for c in range(G):
+                    u = -1 + (2 * c + 2 * t[:, None] + 0 * t[None, :]) / G
+                    v = -1 + (2 * r + 2 * t[None, :] + 0 * t[:, None]) / G
+                    s = u * u + v * v
+                    H = (2 * u * z[0] + 2 * v * z[1] + (s - 1) * z[2]) / (1 + s)
+                    if np.any(np.abs(H) < eps):
+                        assert got["hi"][r, c] == 1
+    a = ov.eps_axis_vote(prob.P, prob.Q, 32, 0.01)
+    b = ov.eps_axis_vote(prob.P, prob.Q, 32, 0.05)
+    assert np.all(a["lo"] <= b["hi"])
+
+
+def test_eps_band_tiny_eps_is_the_curve_test():
+    """eps far below the cell size: the band cells are the closed-cell curve cells (Eq. 9
+    reduces to the curve of Eq. 13 at cell resolution)."""
+    prob = synth.make_problem(80, (0.5,), 0.01, seed=71)
+    G = 64
+    band = ov.eps_axis_vote(prob.P, prob.Q, G, 1e-9)
+    curve = oracle.axis_vote(prob.P, prob.Q, G)
+    both = (band["lo"] == band["hi"]) & (curve["lo"] == curve["hi"])
+    assert np.array_equal(band["grid"][both], curve["grid"][both]) and both.mean() > 0.99
