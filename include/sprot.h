@@ -151,6 +151,15 @@ int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n,
 int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size,
                     uint32_t* grid, void* stream);
 
+/* The consensus accumulator of Eq. 9 at cell resolution: grid[G*G] (device uint32) = the
+ * number of non-degenerate pairs for which some axis r of the closed cell has
+ * |r . z_i| < eps, z_i = (p_i - q_i)/|p_i - q_i| (the cells within angular distance asin(eps)
+ * of the pair's great circle). 0 <= eps < 1; eps = 0 gives the cells the curve crosses
+ * (open test). Overwritten, not accumulated. Errors: E_INVAL (NULL, n < 1, bad G or eps),
+ * E_NOMEM, E_CUDA. */
+int sprot_axis_vote_eps(const float* P, const float* Q, int64_t n, int32_t grid_size, float eps,
+                        uint32_t* grid, void* stream);
+
 /* Least-squares rotation axis of a set of pairs (Eq. 10): the unit r minimising
  * sum_i (z_i . r)^2 over the non-degenerate pairs with labels[i] == label (every pair when
  * labels is NULL), z_i = (p_i - q_i)/|p_i - q_i| -- the eigenvector of S = sum_i z_i z_i^T for

@@ -399,6 +399,29 @@ def eps_axis_vote(P, Q, G: int, eps: float):
     return dict(grid=grid, lo=lo, hi=hi)
 
 
+def eps_cell_votes(P, Q, G: int, eps: float, rows, cols):
+    """Votes of selected cells of the eps-band accumulator over all circles (the test of
+    ``eps_axis_vote`` evaluated cell by cell, for 10^6 circles). Returns (count, lo, hi)."""
+    D, deg = _differences(P, Q)
+    e = grid_edges(G)
+    nd = np.sqrt(np.einsum("ij,ij->i", D, D))
+    cm, cp = D[:, 2] - eps * nd, D[:, 2] + eps * nd
+    out = np.zeros((3, len(rows)), dtype=np.int64)
+    for k, (r, c) in enumerate(zip(rows, cols)):
+        gmin, _ = _quadratic_range(cm, 2.0 * D[:, 0], e[c], e[c + 1])
+        hmin, _ = _quadratic_range(cm, 2.0 * D[:, 1], e[r], e[r + 1])
+        _, gmax = _quadratic_range(cp, 2.0 * D[:, 0], e[c], e[c + 1])
+        _, hmax = _quadratic_range(cp, 2.0 * D[:, 1], e[r], e[r + 1])
+        Fm = gmin + hmin - cp
+        Fp = gmax + hmax - cm
+        voted = (Fm < 0.0) & (Fp > 0.0) & ~deg
+        flag = ((np.abs(Fm) <= BAND * nd) | (np.abs(Fp) <= BAND * nd)) & ~deg
+        out[0, k] = voted.sum()
+        out[1, k] = (voted & ~flag).sum()
+        out[2, k] = (voted | flag).sum()
+    return out[0], out[1], out[2]
+
+
 def ls_axis(P, Q, select=None, hint=None):
     """The least-squares rotation axis of a set of pairs (Eq. 10): the unit r minimising
     sum_i (z_i . r)^2 with z_i = (p_i - q_i)/|p_i - q_i|, i.e. the eigenvector of

@@ -22,7 +22,7 @@ MAX_K = 8
 EXPORTS = [
     "sprot_default_params", "sprot_status_string", "sprot_estimate_rotation",
     "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex", "sprot_axis_vote",
-    "sprot_axis_vote_sampled", "sprot_refine_axis",
+    "sprot_axis_vote_sampled", "sprot_axis_vote_eps", "sprot_refine_axis",
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
                                                 C.POINTER(i32), vp, C.POINTER(Debug), vp]
     lib.sprot_axis_vote.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.sprot_axis_vote_sampled.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+    lib.sprot_axis_vote_eps.argtypes = [vp, vp, i64, i32, C.c_float, vp, vp]
     lib.sprot_refine_axis.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i64), vp]
     lib.sprot_select_peaks.argtypes = [vp, i32, i32, C.c_float, vp, vp, vp, vp]
@@ -127,7 +128,8 @@ def load(path: str = LIB_PATH):
     lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
     lib.sprot_kernel_timing_read.restype = None
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
-                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_refine_axis", "sprot_select_peaks",
+                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_axis_vote_eps", "sprot_refine_axis",
+                 "sprot_select_peaks",
                  "sprot_estimate_batch",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
                  "sprot_server_destroy", "sprot_probe_smem_atomic_rate"]:
@@ -226,6 +228,14 @@ def axis_vote_sampled(P, Q, G: int, J: int, grid, stream=None):
     st = load().sprot_axis_vote_sampled(_ptr(P), _ptr(Q), P.shape[0], int(G), int(J), _ptr(grid),
                                         _stream(stream))
     check(st, "sprot_axis_vote_sampled")
+
+
+def axis_vote_eps(P, Q, G: int, eps: float, grid, stream=None):
+    """Fills the device tensor ``grid`` (G*G 32-bit) with the eps-band accumulator of Eq. 9."""
+    _check_points(P, Q)
+    st = load().sprot_axis_vote_eps(_ptr(P), _ptr(Q), P.shape[0], int(G), float(eps), _ptr(grid),
+                                    _stream(stream))
+    check(st, "sprot_axis_vote_eps")
 
 
 def refine_axis(P, Q, labels=None, label: int = 0, hint=None, stream=None):

@@ -459,8 +459,10 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
 }
 
 // Accumulator only (stage entry point): vote + slice reduction into a caller grid.
+// Accumulator only (stage entry points): the curve vote (eps < 0) or the eps-band vote of
+// Eq. 9 (eps >= 0), then the slice reduction into a caller grid.
 int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* grid,
-                   cudaStream_t st) {
+                   cudaStream_t st, float eps) {
   int status = SPROT_OK;
   Workspace* ws = workspace_for(st, &status);
   if (!ws) return status;
@@ -510,9 +512,13 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   const InstDev* di = reinterpret_cast<InstDev*>(D + o_inst);
   int* dc = reinterpret_cast<int*>(D + o_zero);
   const int nit = (int)vit.size();
-  VoteTimer vt(st);
-  launch_axis_vote_walk(dv, nit, di, dc, std::min(nit, nsm), smem, st);
-  vt.stop(st);
+  if (eps < 0.f) {
+    VoteTimer vt(st);
+    launch_axis_vote_walk(dv, nit, di, dc, std::min(nit, nsm), smem, st);
+    vt.stop(st);
+  } else {
+    launch_axis_vote_eps(dv, nit, di, dc, std::min(nit, nsm), smem, eps, st);
+  }
   launch_grid_reduce(reinterpret_cast<ReduceItem*>(D + o_rit), (int)rit.size(), di, st);
   if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
   // the host staging is reused by the next call: wait for the copy to have been consumed
@@ -633,7 +639,15 @@ int sprot_estimate_rotation(const float* P, const float* Q, int64_t n, const spr
 int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t G, uint32_t* grid, void* stream) {
   if (!P || !Q || !grid || n < 1 || !is_pow2(G) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)
     return SPROT_E_INVAL;
-  return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream));
+  return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream), -1.f);
+}
+
+int sprot_axis_vote_eps(const float* P, const float* Q, int64_t n, int32_t G, float eps, uint32_t* grid,
+                        void* stream) {
+  if (!P || !Q || !grid || n < 1 || n > (int64_t)1 << 31 || !is_pow2(G) || G < SPROT_MIN_GRID ||
+      G > SPROT_MAX_GRID || !(eps >= 0.f && eps < 1.f))
+    return SPROT_E_INVAL;
+  return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream), eps);
 }
 
 int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* labels, int32_t label,

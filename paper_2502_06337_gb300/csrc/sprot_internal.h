@@ -98,6 +98,9 @@ size_t problem_footprint(int64_t n, int G, int J, int k);
 // Axis vote (vote_walk.cu). tile_bytes: the largest band tile of the launch; the kernel adds
 // its per-warp circle tables (vote_table_bytes()) to the dynamic shared memory.
 int vote_table_bytes();
+// eps-band accumulator of Eq. 9 (vote_eps.cu): same items, tiles and partials as the curve vote.
+void launch_axis_vote_eps(const VoteItem* items, int n_items, const InstDev* insts, int* counter, int grid_ctas,
+                          int tile_bytes, float eps, cudaStream_t st);
 // Least-squares axis (post_kernels.cu): FP64 sums of z z^T over the selected pairs in nb chunks
 // of `chunk` pairs into partial[nb][8], then out[6] = axis[3], lambda_min, count, status.
 // hint: host double[3] or NULL.
