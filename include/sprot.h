@@ -106,6 +106,10 @@ const char* sprot_status_string(int status);
 
 /* ---- whole-problem solves ----------------------------------------------------------------- */
 
+/* Every whole-problem solve issues its copies and launches on `stream` as one sequence. With
+ * device pointers (no SPROT_HOST_PTRS, no sprot_debug export) the sequence is captured once
+ * per shape (sizes, item counts, workspace) as a CUDA graph and replayed on later calls. */
+
 /* Single rotation (Algorithm 1 end to end plus refinement).
  *   P, Q         n x 3 float32 (device, or host with SPROT_HOST_PTRS)
  *   n            number of correspondences, >= 1

@@ -260,25 +260,114 @@ def select_peaks(grid, G: int, k: int, nms_deg: float, cells, counts, n_found, s
     check(st, "sprot_select_peaks")
 
 
+def _struct_dtype(ctype, prefix="", base=0, out=None):
+    """numpy dtype fields (name, format, offset) of a ctypes structure, flattened."""
+    out = [] if out is None else out
+    for name, t in ctype._fields_:
+        off = base + getattr(ctype, name).offset
+        if isinstance(t, type) and issubclass(t, C.Structure):
+            _struct_dtype(t, prefix + name + ".", off, out)
+        else:
+            fmt = {C.c_int32: "<i4", C.c_uint32: "<u4", C.c_int64: "<i8", C.c_float: "<f4",
+                   C.c_double: "<f8"}.get(t, "<u8")  # pointers: 64-bit addresses
+            out.append((prefix + name, fmt, off))
+    return out
+
+
+_INSTANCE_FIELDS = None
+_ROTATION_DTYPE = None
+
+
+def _rotation_dtype():
+    global _ROTATION_DTYPE
+    if _ROTATION_DTYPE is None:
+        f = []
+        for name, t in Rotation._fields_:
+            off = getattr(Rotation, name).offset
+            if name in ("R", "R_init", "R_vote"):
+                f.append((name, ("<f8", (9,)), off))
+            elif name == "axis":
+                f.append((name, ("<f8", (3,)), off))
+            else:
+                f.append((name, {C.c_double: "<f8", C.c_int32: "<i4", C.c_uint32: "<u4"}[t], off))
+        _ROTATION_DTYPE = np.dtype({"names": [x[0] for x in f], "formats": [x[1] for x in f],
+                                    "offsets": [x[2] for x in f], "itemsize": C.sizeof(Rotation)})
+    return _ROTATION_DTYPE
+
+
+class BatchResult:
+    """Rotations of a batched solve, kept as one array; res[i] is the list of rotation dicts of
+    instance i (built on access)."""
+
+    def __init__(self, rot: np.ndarray, n_found: np.ndarray, kmax: int):
+        self.rot = rot.reshape(len(n_found), kmax)
+        self.n_found = n_found
+
+    def __len__(self):
+        return len(self.n_found)
+
+    def _one(self, i):
+        out = []
+        for a in range(int(self.n_found[i])):
+            r = self.rot[i, a]
+            out.append(dict(R=r["R"].reshape(3, 3).copy(), R_init=r["R_init"].reshape(3, 3).copy(),
+                            R_vote=r["R_vote"].reshape(3, 3).copy(), axis=r["axis"].copy(),
+                            theta=float(r["theta"]), cell=(int(r["cell_row"]), int(r["cell_col"])),
+                            bin=int(r["angle_bin"]), axis_votes=int(r["axis_votes"]),
+                            angle_votes=int(r["angle_votes"]), n_vote_set=int(r["n_vote_set"]),
+                            n_inliers=int(r["n_inliers"]), n_degenerate=int(r["n_degenerate"])))
+        return out
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self._one(j) for j in range(*i.indices(len(self)))]
+        return self._one(i if i >= 0 else len(self) + i)
+
+    def __iter__(self):
+        return (self._one(i) for i in range(len(self)))
+
+
 def estimate_batch(problems, stream=None):
-    """problems: list of (P, Q, Params[, labels]) with device tensors. Returns (list of
-    rotation lists, list of the grid sides used)."""
+    """problems: list of (P, Q, Params[, labels]) with device tensors. Returns (BatchResult,
+    array of the grid sides used). The instance table is built as one numpy record array in
+    the layout of sprot_instance, so that a batch of thousands costs no per-field Python work."""
+    global _INSTANCE_FIELDS
     lib = load()
+    if _INSTANCE_FIELDS is None:
+        _INSTANCE_FIELDS = _struct_dtype(Instance)
     m = len(problems)
-    insts = (Instance * m)()
-    keep = []
+    fields = _INSTANCE_FIELDS
+    dt = np.dtype({"names": [f[0] for f in fields], "formats": [f[1] for f in fields],
+                   "offsets": [f[2] for f in fields], "itemsize": C.sizeof(Instance)})
+    tab = np.zeros(m, dtype=dt)
+    kmax = 1
+    for pb in problems:
+        kmax = max(kmax, int(pb[2].k))
+    rot = np.zeros(m * kmax, dtype=_rotation_dtype())
+    n_found = np.zeros(m, dtype=np.int32)
+    P_ptr = np.empty(m, dtype=np.uint64)
+    Q_ptr = np.empty(m, dtype=np.uint64)
+    L_ptr = np.zeros(m, dtype=np.uint64)
+    ns = np.empty(m, dtype=np.int64)
+    prm_cols = {name: np.empty(m, dtype=dt.fields["params." + name][0]) for name, _ in Params._fields_}
     for i, pb in enumerate(problems):
         P, Q, prm = pb[0], pb[1], pb[2]
-        labels = pb[3] if len(pb) > 3 else None
         _check_points(P, Q)
-        outs = (Rotation * max(1, prm.k))()
-        nf = C.c_int32(0)
-        keep.append((outs, nf))
-        insts[i] = Instance(_ptr(P), _ptr(Q), P.shape[0], prm, outs, C.pointer(nf), _ptr(labels))
-    st = lib.sprot_estimate_batch(insts, m, _stream(stream))
+        P_ptr[i] = P.data_ptr()
+        Q_ptr[i] = Q.data_ptr()
+        ns[i] = P.shape[0]
+        if len(pb) > 3 and pb[3] is not None:
+            L_ptr[i] = pb[3].data_ptr()
+        for name, _ in Params._fields_:
+            prm_cols[name][i] = getattr(prm, name)
+    tab["P"], tab["Q"], tab["n"], tab["labels"] = P_ptr, Q_ptr, ns, L_ptr
+    for name, col in prm_cols.items():
+        tab["params." + name] = col
+    tab["out"] = rot.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(kmax * C.sizeof(Rotation))
+    tab["n_found"] = n_found.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(4)
+    st = lib.sprot_estimate_batch(tab.ctypes.data_as(C.POINTER(Instance)), m, _stream(stream))
     check(st, "sprot_estimate_batch")
-    res = [[outs[a].to_dict() for a in range(nf.value)] for outs, nf in keep]
-    return res, [insts[i].params.grid for i in range(m)]
+    return BatchResult(rot, n_found, kmax), tab["params.grid"].copy()
 
 
 class Server:

@@ -62,9 +62,9 @@ __device__ __forceinline__ bool suppressed(const CellAxis& c, const CellAxis& p,
   return dot >= cosr * (c.N * p.N);
 }
 
-// Sum of the slice partials of kReduceWords accumulator words: one 16-byte column (4 words,
-// 8 cells) per thread, the S slices loaded several at a time, then the grid and the largest
-// peak key of the item.
+// Sum of the slice partials of an item of accumulator words: one 16-byte column (4 words,
+// 8 cells) per thread and pass, the S slices loaded several at a time, then the grid and the
+// largest peak key of the item.
 __global__ void __launch_bounds__(kReduceWords / 4)
     k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
   const ReduceItem I = items[blockIdx.x];
@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(kReduceWords / 4)
   const int G = D.G, W = G >> 1, S = D.S;
   const int64_t plane = (int64_t)G * W;
   unsigned long long best = 0;
-  const int64_t w = I.w0 + 4 * threadIdx.x;  // words w .. w+3 lie in one row (W % 4 == 0)
-  if (w < I.w1) {
+  // words w .. w+3 lie in one row (W % 4 == 0); an item may span several passes of the block
+  for (int64_t w = I.w0 + 4 * threadIdx.x; w < I.w1; w += 4 * blockDim.x) {
     uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint4* p = reinterpret_cast<const uint4*>(D.partial + w);
     const int64_t stride = plane / 4;

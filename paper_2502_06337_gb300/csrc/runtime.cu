@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <optional>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -141,6 +142,15 @@ struct InstPlan {
   size_t o_nfound, o_rot;          // result region
 };
 
+// An instantiated CUDA graph of one solve's launch sequence and the number of kernels in it
+// (exec = nullptr: the shape could not be captured and runs directly).
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
+  int uses = 0;            // calls seen with this shape
+  bool capturable = true;  // false after a failed capture
+};
+
 struct Workspace {
   std::mutex mu;
   int device = 0;
@@ -148,11 +158,31 @@ struct Workspace {
   size_t dev_cap = 0;
   char* host = nullptr;  // pinned
   size_t host_cap = 0;
+  // Graphs keyed by everything a captured sequence bakes in: workspace addresses, copy sizes,
+  // grid sizes and item counts (the tables themselves are re-uploaded by the graph).
+  std::map<std::vector<uint64_t>, GraphEntry> graphs;
+  // events recorded around the vote kernel inside every captured sequence (solves on a
+  // workspace are serialised and synchronised, so one pair serves all its graphs)
+  cudaEvent_t tv0 = nullptr, tv1 = nullptr;
+  bool timing_events() {
+    if (!tv0 && cudaEventCreate(&tv0) != cudaSuccess) tv0 = nullptr;
+    if (!tv1 && cudaEventCreate(&tv1) != cudaSuccess) tv1 = nullptr;
+    return tv0 && tv1;
+  }
+  void drop_graphs() {
+    for (auto& kv : graphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
   ~Workspace() {
+    drop_graphs();
+    if (tv0) cudaEventDestroy(tv0);
+    if (tv1) cudaEventDestroy(tv1);
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
   int reserve(size_t dbytes, size_t hbytes) {
+    if (dbytes > dev_cap || hbytes > host_cap) drop_graphs();  // their addresses are about to change
     if (dbytes > dev_cap) {
       size_t want = std::max(dbytes, dev_cap + dev_cap / 2);
       if (dev) cudaFree(dev);
@@ -203,8 +233,17 @@ Workspace* workspace_for(cudaStream_t st, int* status) {
   return slot.get();
 }
 
+// Pairs per work item of the per-pair kernels. One problem: about 600 items, so that the
+// problem alone fills the GPU. A batch: sized from the batch's total (the instances provide the
+// parallelism), so that small instances do not pay a block's fixed cost per few hundred pairs.
 int stream_chunk(int64_t n) {
   int64_t c = (n + 599) / 600;
+  c = (c + 255) / 256 * 256;
+  return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
+}
+
+int batch_chunk(int64_t total) {
+  int64_t c = (total + 1199) / 1200;
   c = (c + 255) / 256 * 256;
   return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
 }
@@ -239,8 +278,53 @@ size_t problem_footprint(int64_t n, int G, int J, int k) {
          align_up((size_t)k * J * 4) + align_up(sizeof(DevRot) * k) + 4096;
 }
 
+// Runs `enqueue` (which issues one solve's asynchronous work on st) through the graph cached
+// under `key`. A shape is captured when it is seen for the second time (shapes that never
+// repeat, as in a server's mixed batches, are not worth a capture and instantiation); a shape
+// that cannot be captured runs directly from then on. Returns enqueue's success (or the graph
+// launch's).
+template <class F>
+bool run_graph(Workspace* ws, const std::vector<uint64_t>& key, cudaStream_t st, F&& enqueue) {
+  auto it = ws->graphs.find(key);
+  if (it == ws->graphs.end()) {
+    if (ws->graphs.size() >= 64) ws->drop_graphs();
+    ws->graphs[key].uses = 1;
+    return enqueue();
+  }
+  GraphEntry& ge = it->second;
+  if (ge.exec) {
+    if (cudaGraphLaunch(ge.exec, st) != cudaSuccess) return false;
+    launches_add(ge.kernels);
+    return true;
+  }
+  if (!ge.capturable || ++ge.uses < 2) return enqueue();
+  const uint64_t l0 = launches_add(0);
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ge.capturable = false;
+    return enqueue();
+  }
+  const bool ok = enqueue();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  const uint64_t kernels = launches_add(0) - l0;
+  cudaGraphExec_t ex = nullptr;
+  if (!ok || e != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    launches_add(0 - kernels);  // captured launches that never ran
+    ge.capturable = false;
+    return enqueue();
+  }
+  cudaGraphDestroy(g);
+  ge.exec = ex;
+  ge.kernels = kernels;
+  // the captured launches were counted once: they stand for this first execution
+  return cudaGraphLaunch(ex, st) == cudaSuccess;
+}
+
 // Solves a batch of problems on stream st. Every Problem must be validated already.
-int solve(std::vector<Problem>& probs, cudaStream_t st) {
+int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   const int m = (int)probs.size();
   int status = SPROT_OK;
   Workspace* ws = workspace_for(st, &status);
@@ -250,6 +334,11 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
 
   // ---- plan ---------------------------------------------------------------------------
   std::vector<InstPlan> plan(m);
+  int64_t total_n = 0;
+  for (int i = 0; i < m; ++i) total_n += probs[i].n;
+  // slice-reduction items: 512 words (one 16-byte column per thread) for one problem; in a
+  // batch about 64 x 512 word-slices per item (an item reads every slice of its words), between
+  // 512 and 8192 words
   std::vector<VoteItem> vitems;
   int vote_tile = 0;
   std::vector<ReduceItem> ritems;
@@ -274,9 +363,12 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
       for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
     }
     int64_t words = (int64_t)ip.G * (ip.G / 2);
-    for (int64_t w0 = 0; w0 < words; w0 += kReduceWords)
-      ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + kReduceWords, words)});
-    ip.chunk = stream_chunk(pb.n);
+    const int64_t red_words =
+        m == 1 ? kReduceWords
+               : kReduceWords * std::min<int64_t>(16, std::max<int64_t>(1, 64 / std::max(ip.S, 1)));
+    for (int64_t w0 = 0; w0 < words; w0 += red_words)
+      ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + red_words, words)});
+    ip.chunk = m == 1 ? stream_chunk(pb.n) : batch_chunk(total_n);
     ip.item0 = (int)sitems.size();
     for (int64_t a = 0; a < pb.n; a += ip.chunk)
       sitems.push_back(StreamItem{i, 0, a, std::min<int64_t>(a + ip.chunk, pb.n)});
@@ -379,55 +471,86 @@ int solve(std::vector<Problem>& probs, cudaStream_t st) {
   std::memcpy(H + o_rit, ritems.data(), sizeof(ReduceItem) * ritems.size());
   std::memcpy(H + o_sit, sitems.data(), sizeof(StreamItem) * sitems.size());
 
-  // ---- launches -----------------------------------------------------------------------
+  // ---- launches (replayed from a cached CUDA graph when the shape repeats) ----------------
   auto ck = [](cudaError_t e) { return e == cudaSuccess; };
-  bool ok = true;
-  ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
-  ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
-  for (int i = 0; i < m; ++i) {
-    const Problem& pb = probs[i];
-    if (pb.dbg && pb.dbg->hist)
-      ok &= ck(cudaMemsetAsync(pb.dbg->hist, 0, sizeof(uint32_t) * plan[i].k * plan[i].J, st));
-    if (pb.host_io) {
-      ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
-      ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
-    }
-  }
-  if (!ok) return SPROT_E_CUDA;
   const InstDev* dinst = reinterpret_cast<const InstDev*>(D + o_inst);
   const VoteItem* dvit = reinterpret_cast<const VoteItem*>(D + o_vit);
   const ReduceItem* drit = reinterpret_cast<const ReduceItem*>(D + o_rit);
   const StreamItem* dsit = reinterpret_cast<const StreamItem*>(D + o_sit);
   int* dcounter = reinterpret_cast<int*>(D + o_counter);
-  VoteTimer vt(st);
-  launch_axis_vote_walk(dvit, (int)vitems.size(), dinst, dcounter,
-                        std::min((int)vitems.size(), nsm), vote_tile, st);
-  vt.stop(st);
-  launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
-  for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
-  launch_finalize_peaks(dinst, m, st);
-  launch_angle_vote(dsit, (int)sitems.size(), dinst, max_k, max_J, st);
-  launch_angle_peak(dinst, m, max_k, st);
-  launch_vote_set_sum(dsit, (int)sitems.size(), dinst, max_k, st);
-  launch_kabsch(dinst, m, max_k, 0, st);
-  launch_label_sum(dsit, (int)sitems.size(), dinst, max_k, st);
-  launch_kabsch(dinst, m, max_k, 1, st);
-  if (!ck(cudaGetLastError())) return SPROT_E_CUDA;
-
-  // ---- results ------------------------------------------------------------------------
   char* Hres = H + align_up(header_end);
-  ok &= ck(cudaMemcpyAsync(Hres, D + o_res, res_end - o_res, cudaMemcpyDeviceToHost, st));
-  for (int i = 0; i < m; ++i) {
-    const Problem& pb = probs[i];
-    if (!pb.host_io) continue;
-    if (pb.labels)
-      ok &= ck(cudaMemcpyAsync(pb.labels, D + plan[i].o_labels, (size_t)pb.n * 4,
-                               cudaMemcpyDeviceToHost, st));
-    if (pb.mask)
-      ok &= ck(cudaMemcpyAsync(pb.mask, D + plan[i].o_mask, (size_t)pb.n, cudaMemcpyDeviceToHost, st));
+  // caller pointers outside the workspace (debug exports, host inputs) would be baked into a
+  // graph: those calls run directly
+  bool direct_only = !graphs || !ws->timing_events();
+  for (int i = 0; i < m; ++i) direct_only |= probs[i].dbg != nullptr || probs[i].host_io;
+  std::optional<VoteTimer> vt;
+  auto enqueue = [&](bool direct) -> bool {
+    bool ok = true;
+    ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
+    ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
+    for (int i = 0; i < m; ++i) {
+      const Problem& pb = probs[i];
+      if (pb.dbg && pb.dbg->hist)
+        ok &= ck(cudaMemsetAsync(pb.dbg->hist, 0, sizeof(uint32_t) * plan[i].k * plan[i].J, st));
+      if (pb.host_io) {
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
+      }
+    }
+    if (!ok) return false;
+    if (direct)
+      vt.emplace(st);
+    else
+      ok &= ck(cudaEventRecord(ws->tv0, st));
+    launch_axis_vote_walk(dvit, (int)vitems.size(), dinst, dcounter,
+                          std::min((int)vitems.size(), nsm), vote_tile, st);
+    if (direct)
+      vt->stop(st);
+    else
+      ok &= ck(cudaEventRecord(ws->tv1, st));
+    launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
+    for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
+    launch_finalize_peaks(dinst, m, st);
+    launch_angle_vote(dsit, (int)sitems.size(), dinst, max_k, max_J, st);
+    launch_angle_peak(dinst, m, max_k, st);
+    launch_vote_set_sum(dsit, (int)sitems.size(), dinst, max_k, st);
+    launch_kabsch(dinst, m, max_k, 0, st);
+    launch_label_sum(dsit, (int)sitems.size(), dinst, max_k, st);
+    launch_kabsch(dinst, m, max_k, 1, st);
+    if (!ck(cudaGetLastError())) return false;
+    ok &= ck(cudaMemcpyAsync(Hres, D + o_res, res_end - o_res, cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < m; ++i) {
+      const Problem& pb = probs[i];
+      if (!pb.host_io) continue;
+      if (pb.labels)
+        ok &= ck(cudaMemcpyAsync(pb.labels, D + plan[i].o_labels, (size_t)pb.n * 4,
+                                 cudaMemcpyDeviceToHost, st));
+      if (pb.mask)
+        ok &= ck(cudaMemcpyAsync(pb.mask, D + plan[i].o_mask, (size_t)pb.n, cudaMemcpyDeviceToHost, st));
+    }
+    return ok;
+  };
+  bool ok;
+  if (direct_only) {
+    ok = enqueue(true);
+  } else {
+    const std::vector<uint64_t> key = {
+        (uint64_t)(uintptr_t)D, (uint64_t)(uintptr_t)H, header_end, o_zero, zero_end, o_res, res_end,
+        vitems.size(), ritems.size(), sitems.size(), (uint64_t)m, (uint64_t)max_k, (uint64_t)max_J,
+        (uint64_t)vote_tile, (uint64_t)nsm};
+    ok = run_graph(ws, key, st, [&] { return enqueue(false); });
   }
   if (!ok || !ck(cudaStreamSynchronize(st))) return SPROT_E_CUDA;
-  vt.collect();
+  if (vt) {
+    vt->collect();
+  } else if (g_timing.load()) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ws->tv0, ws->tv1) == cudaSuccess) {
+      std::lock_guard<std::mutex> g(g_timing_mu);
+      g_vote_ms += ms;
+      g_vote_launches += 1;
+    }
+  }
   int worst = SPROT_OK;
   for (int i = 0; i < m; ++i) {
     const InstPlan& ip = plan[i];

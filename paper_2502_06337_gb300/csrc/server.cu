@@ -135,7 +135,8 @@ void sprot_server::worker_main(int idx) {
                                 nullptr, nullptr});
       }
     }
-    if (status == SPROT_OK) status = solve(probs, st);
+    // mixed batches rarely repeat a shape: no graph capture on the serving path
+    if (status == SPROT_OK) status = solve(probs, st, false);
     {
       std::lock_guard<std::mutex> g(mu);
       double t = now_ms();

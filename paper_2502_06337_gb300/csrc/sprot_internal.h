@@ -89,7 +89,8 @@ struct Problem {
 
 // Solves the problems (validated by the caller) with one launch sequence on st and waits for
 // the results. Returns SPROT_OK, or for a single problem SPROT_E_NOAXIS when it has no peak.
-int solve(std::vector<Problem>& probs, cudaStream_t st);
+// graphs: replay the launch sequence from a CUDA graph when its shape repeats (see runtime.cu)
+int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true);
 
 // Device bytes one problem occupies in a solve() workspace (inputs excluded).
 size_t problem_footprint(int64_t n, int G, int J, int k);

@@ -21,8 +21,8 @@ def _same(a, b, tol=1e-12):
     for x, y in zip(a, b):
         for key in INT_KEYS:
             assert x[key] == y[key], (key, x[key], y[key])
-        assert parity.rot_diff(x["R"], y["R"]) < tol
-        assert parity.rot_diff(x["R_init"], y["R_init"]) < tol
+        assert parity.rot_diff(x["R"], y["R"]) <= tol
+        assert parity.rot_diff(x["R_init"], y["R_init"]) <= tol
 
 
 def _instances():
@@ -144,3 +144,30 @@ def test_server_admission_and_invalid_requests(lib):
         with pytest.raises(B.SprotError) as e:
             srv.wait(t + 1000)  # no such ticket
         assert e.value.status == B.E_INVAL
+
+
+def test_graph_replay_matches_direct_solves(lib):
+    """Two problems of the same shape solved alternately (the shape is captured as a CUDA graph
+    on its second call and replayed after): every result equals the direct solve of the same
+    problem (the debug-export path, which never uses graphs)."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    probs = [synth.make_problem(30000, (0.2,), 0.01, seed=s) for s in (31, 32)]
+    dev = [(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda()) for p in probs]
+    prm = B.make_params(grid=256, angle_bins=360, tau=0.05)
+    direct = []
+    for P, Q in dev:
+        dbg = dict(grid=torch.zeros(256 * 256, dtype=torch.int32, device="cuda"))
+        direct.append(B.estimate_rotations(P, Q, prm, debug=dbg))
+    for rep in range(3):
+        for (P, Q), want in zip(dev, direct):
+            _same(B.estimate_rotations(P, Q, prm), want, tol=0.0)
+    # a batch shape repeated: the graph replays with new tables
+    batch = [(P, Q, prm) for P, Q in dev]
+    first, _ = B.estimate_batch(batch)
+    for rep in range(2):
+        again, _ = B.estimate_batch(batch[::-1])
+        _same(again[0], first[1], tol=0.0)
+        _same(again[1], first[0], tol=0.0)
