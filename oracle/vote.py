@@ -347,19 +347,28 @@ def refine(P, Q, V, R_fallback, tau: float):
 def assign_labels(P, Q, R1s, tau: float):
     """Labels for several rotations: pair i goes to the rotation a with the smallest
     residual ||q_i - R1_a p_i|| among those <= tau (ties to the smaller a), else -1.
-    Returns (labels, flag) with flag set where any residual is within the band of tau."""
+    Returns (labels, flag). A pair is flagged where any residual is within the band of tau,
+    or where two residuals <= tau are within the band of each other (the choice between the
+    two rotations is then a float decision at its threshold, as when two found rotations
+    approximate the same true one)."""
     P = np.asarray(P, dtype=np.float64)
     Q = np.asarray(Q, dtype=np.float64)
     scale = BAND * (1.0 + np.linalg.norm(P, axis=1) + np.linalg.norm(Q, axis=1))
     best = np.full(P.shape[0], np.inf)
     labels = np.full(P.shape[0], -1, dtype=np.int32)
     flag = np.zeros(P.shape[0], dtype=bool)
+    within = []
     for a, R1 in enumerate(R1s):
         res = np.linalg.norm(Q - P @ np.asarray(R1).T, axis=1)
         flag |= np.abs(res - tau) <= scale
+        within.append(np.where(res <= tau + scale, res, np.inf))
         take = (res <= tau) & (res < best)
         labels[take] = a
         best[take] = res[take]
+    if len(within) > 1:
+        w = np.sort(np.stack(within, axis=1), axis=1)
+        two = np.isfinite(w[:, 1])
+        flag[two] |= w[two, 1] - w[two, 0] <= scale[two]
     return labels, flag
 
 
