@@ -370,6 +370,26 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Warp sums of 16 per-lane doubles by recursive halving: at each level a lane keeps half of
+// its values and adds the partner lane's copies of them, so the 16 sums cost 8 + 4 + 2 + 1 + 1
+// FP64 additions per lane instead of 5 per value (FP64 instructions are scarce on this part:
+// about two lanes per clock per SM). Lane l returns the total of value (l >> 1) & 15.
+__device__ __forceinline__ double warp_sum16(const double (&v)[16], int lane) {
+  double a8[8], a4[4], a2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    a8[j] = (h16 ? v[8 + j] : v[j]) + __shfl_xor_sync(kFull, h16 ? v[j] : v[8 + j], 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    a4[j] = (h8 ? a8[4 + j] : a8[j]) + __shfl_xor_sync(kFull, h8 ? a8[j] : a8[4 + j], 8);
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    a2[j] = (h4 ? a4[2 + j] : a4[j]) + __shfl_xor_sync(kFull, h4 ? a4[j] : a4[2 + j], 4);
+  double a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(kFull, h2 ? a2[0] : a2[1], 2);
+  return a1 + __shfl_xor_sync(kFull, a1, 1);
+}
+
 // Block sum of acc[K][10] into out[kf][10] (fixed order: warps in index order). All threads
 // call; the rotation loop is unrolled so that acc stays in registers.
 template <int K>
@@ -379,11 +399,11 @@ __device__ __forceinline__ void block_sums(double (&acc)[K][10], int kf, double*
 #pragma unroll
   for (int a = 0; a < K; ++a) {
     if (a >= kf) break;
+    double v16[16];
 #pragma unroll
-    for (int t = 0; t < 10; ++t) {
-      double v = warp_sum_d(acc[a][t]);
-      if (l == 0) s[w][t] = v;
-    }
+    for (int t = 0; t < 16; ++t) v16[t] = t < 10 ? acc[a][t] : 0.0;
+    const double tot = warp_sum16(v16, l);
+    if ((l & 1) == 0 && (l >> 1) < 10) s[w][l >> 1] = tot;
     __syncthreads();
     if (threadIdx.x < 10) {
       double v = 0;
@@ -932,11 +952,11 @@ __global__ void __launch_bounds__(kAxisThreads)
   }
   __syncwarp();
   if (lane < len) add(i0 + queue[wp][lane]);
+  double v16[16];
 #pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    const double v = warp_sum_d(acc[t]);
-    if (lane == 0) red[wp][t] = v;
-  }
+  for (int t = 0; t < 16; ++t) v16[t] = t < 6 ? acc[t] : 0.0;
+  const double tot = warp_sum16(v16, lane);
+  if ((lane & 1) == 0 && (lane >> 1) < 6) red[wp][lane >> 1] = tot;
   if (lane == 0) red[wp][6] = (double)total;
   __syncthreads();
   if (threadIdx.x < 7) {
