@@ -100,6 +100,17 @@ def test_multi_rotation_parity(lib):
         assert min(oracle.rotation_error(Rg, r["R"]) for r in g["rots"]) < math.radians(0.5)
 
 
+def test_maximum_k_and_angle_bins(lib):
+    """The largest k (8) and J (4096): eight rotations owning 10 % each, every stage in full
+    (the K = 8 instances of the per-pair kernels and the widest angle histogram)."""
+    prob = synth.make_problem(6000, (0.1,) * 8, 0.002, seed=23)
+    G, J = 128, 4096
+    g = parity.run_gpu(prob.P, prob.Q, G, J, k=8, nms=3.0)
+    av = oracle.axis_vote(prob.P, prob.Q, G)
+    parity.check_solve(prob.P, prob.Q, g, G, J, k=8, nms=3.0, av=av)
+    assert len(g["rots"]) == 8
+
+
 def test_select_peaks_on_constructed_grid(lib):
     import torch
 
