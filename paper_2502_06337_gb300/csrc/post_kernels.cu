@@ -65,6 +65,48 @@ __device__ __forceinline__ bool suppressed(const CellAxis& c, const CellAxis& p,
 // Sum of the slice partials of an item of accumulator words: one 16-byte column (4 words,
 // 8 cells) per thread and pass, the S slices loaded several at a time, then the grid and the
 // largest peak key of the item.
+// Last-block election on a per-instance stage counter: every thread of the block calls it
+// after its own writes (each thread fences them); the block whose arrival completes `target`
+// gets true in all its threads and may then read every other block's results. No block waits
+// on another: the last one to arrive does the instance's remaining work.
+__device__ __forceinline__ bool last_block(uint32_t* counter, uint32_t target) {
+  __shared__ uint32_t s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) + 1u == target ? 1u : 0u;
+  __syncthreads();
+  const bool last = s_last != 0u;
+  if (last) __threadfence();
+  return last;
+}
+
+// The instance's peaks (thread 0): axes by Eq. 12 at the cell centres (exact integer
+// geometry), canonical r_z <= 0, and the number found.
+__device__ void finalize_instance(const InstDev& D) {
+  int found = 0;
+  for (int a = 0; a < D.k; ++a) {
+    const unsigned long long key = __ldcg(D.peak_key + a);
+    if (!key) break;
+    const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
+    const int row = idx / D.G, col = idx % D.G;
+    DevRot& R = D.rot[a];
+    const CellAxis c = cell_axis(D.G, row, col);
+    const double sgn = c.w2 > 0 ? -1.0 : 1.0;  // canonical: southern hemisphere, r_z <= 0
+    const double r0 = sgn * c.w0 / c.N, r1 = sgn * c.w1 / c.N, r2 = sgn * c.w2 / c.N;
+    R.axis[0] = r0;
+    R.axis[1] = r1;
+    R.axis[2] = r2;
+    R.r_cell[0] = (float)r0;
+    R.r_cell[1] = (float)r1;
+    R.r_cell[2] = (float)r2;
+    R.cell_row = row;
+    R.cell_col = col;
+    R.axis_votes = (uint32_t)(key >> 32);
+    ++found;
+  }
+  *D.n_found = found;
+}
+
 __global__ void __launch_bounds__(kReduceWords / 4)
     k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
   const ReduceItem I = items[blockIdx.x];
@@ -123,6 +165,9 @@ __global__ void __launch_bounds__(kReduceWords / 4)
   }
   best = block_max_u64(best);
   if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[0], best);
+  // the last item of the instance (of the last suppression round when k > 1) finalises
+  if (D.done && last_block(&D.done[0], (uint32_t)(D.n_ritems * D.k)) && threadIdx.x == 0)
+    finalize_instance(D);
 }
 
 __global__ void __launch_bounds__(256)
@@ -132,7 +177,11 @@ __global__ void __launch_bounds__(256)
   if (round >= D.k) return;
   __shared__ CellAxis taken[kMaxK];
   const int G = D.G, W = G >> 1;
-  if (round > 0 && D.peak_key[round - 1] == 0) return;  // fewer peaks than asked for
+  if (round > 0 && D.peak_key[round - 1] == 0) {  // fewer peaks than asked for
+    if (D.done && last_block(&D.done[0], (uint32_t)(D.n_ritems * D.k)) && threadIdx.x == 0)
+      finalize_instance(D);
+    return;
+  }
   if (threadIdx.x < round) {
     unsigned long long key = D.peak_key[threadIdx.x];
     uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
@@ -158,34 +207,46 @@ __global__ void __launch_bounds__(256)
   }
   best = block_max_u64(best);
   if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[round], best);
+  if (D.done && last_block(&D.done[0], (uint32_t)(D.n_ritems * D.k)) && threadIdx.x == 0)
+    finalize_instance(D);
 }
 
-__global__ void k_finalize_peaks(const InstDev* __restrict__ insts, int m) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  const InstDev& D = insts[i];
-  int found = 0;
-  for (int a = 0; a < D.k; ++a) {
-    unsigned long long key = D.peak_key[a];
-    if (!key) break;
-    uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
-    int row = idx / D.G, col = idx % D.G;
-    DevRot& R = D.rot[a];
-    CellAxis c = cell_axis(D.G, row, col);
-    double sgn = c.w2 > 0 ? -1.0 : 1.0;  // canonical: southern hemisphere, r_z <= 0
-    double r0 = sgn * c.w0 / c.N, r1 = sgn * c.w1 / c.N, r2 = sgn * c.w2 / c.N;
-    R.axis[0] = r0;
-    R.axis[1] = r1;
-    R.axis[2] = r2;
-    R.r_cell[0] = (float)r0;
-    R.r_cell[1] = (float)r1;
-    R.r_cell[2] = (float)r2;
-    R.cell_row = row;
-    R.cell_col = col;
-    R.axis_votes = (uint32_t)(key >> 32);
-    ++found;
+// Peak bin of the histogram of rotation a, the bin-centre angle and R_vote by Rodrigues
+// (Eq. 2). Called by a whole block.
+__device__ void angle_peak_block(const InstDev& D, int a) {
+  const int J = D.J;
+  const uint32_t* h = D.hist + (int64_t)a * J;
+  unsigned long long best = 0;
+  for (int b = threadIdx.x; b < J; b += blockDim.x) {
+    unsigned long long key = ((unsigned long long)__ldcg(h + b) << 32) | (0xffffffffu - (uint32_t)b);
+    best = key > best ? key : best;
   }
-  *D.n_found = found;
+  best = block_max_u64(best);
+  if (threadIdx.x != 0) return;
+  DevRot& R = D.rot[a];
+  int b = (int)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
+  R.angle_bin = b;
+  R.angle_votes = (uint32_t)(best >> 32);
+  double th = -CUDART_PI + (b + 0.5) * (2.0 * CUDART_PI / J);
+  double r0 = R.axis[0], r1 = R.axis[1], r2 = R.axis[2];
+  if (th < 0) {
+    th = -th;
+    r0 = -r0;
+    r1 = -r1;
+    r2 = -r2;
+  }
+  R.axis[0] = r0;
+  R.axis[1] = r1;
+  R.axis[2] = r2;
+  R.theta = th;
+  double s = sin(th), c1 = 1.0 - cos(th);
+  // K = [r]_x ; R = I + s K + (1 - cos) K^2, K^2 = r r^T - I
+  double K[9] = {0, -r2, r1, r2, 0, -r0, -r1, r0, 0};
+  double rr[3] = {r0, r1, r2};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      R.R_vote[3 * i + j] = (i == j ? 1.0 : 0.0) + s * K[3 * i + j] +
+                            c1 * (rr[i] * rr[j] - (i == j ? 1.0 : 0.0));
 }
 
 // ---- angle vote ------------------------------------------------------------------------
@@ -320,47 +381,16 @@ __global__ void __launch_bounds__(kStreamThreads)
     if (v) atomicAdd(&D.hist[t], v);
   }
   if (threadIdx.x == 0 && s_deg) atomicAdd(D.n_deg, s_deg);
+  // the last item of the instance takes the peak bins
+  if (D.done && last_block(&D.done[1], (uint32_t)D.n_items)) {
+    for (int a = 0; a < kf; ++a) {
+      angle_peak_block(D, a);
+      __syncthreads();
+    }
+  }
 }
 
-// Peak bin of each histogram, the bin-centre angle and R_vote by Rodrigues (Eq. 2).
-__global__ void __launch_bounds__(256) k_angle_peak(const InstDev* __restrict__ insts, int max_k) {
-  const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
-  const InstDev& D = insts[inst];
-  if (a >= *D.n_found) return;
-  const int J = D.J;
-  const uint32_t* h = D.hist + (int64_t)a * J;
-  unsigned long long best = 0;
-  for (int b = threadIdx.x; b < J; b += blockDim.x) {
-    unsigned long long key = ((unsigned long long)h[b] << 32) | (0xffffffffu - (uint32_t)b);
-    best = key > best ? key : best;
-  }
-  best = block_max_u64(best);
-  if (threadIdx.x != 0) return;
-  DevRot& R = D.rot[a];
-  int b = (int)(0xffffffffu - (uint32_t)(best & 0xffffffffu));
-  R.angle_bin = b;
-  R.angle_votes = (uint32_t)(best >> 32);
-  double th = -CUDART_PI + (b + 0.5) * (2.0 * CUDART_PI / J);
-  double r0 = R.axis[0], r1 = R.axis[1], r2 = R.axis[2];
-  if (th < 0) {
-    th = -th;
-    r0 = -r0;
-    r1 = -r1;
-    r2 = -r2;
-  }
-  R.axis[0] = r0;
-  R.axis[1] = r1;
-  R.axis[2] = r2;
-  R.theta = th;
-  double s = sin(th), c1 = 1.0 - cos(th);
-  // K = [r]_x ; R = I + s K + (1 - cos) K^2, K^2 = r r^T - I
-  double K[9] = {0, -r2, r1, r2, 0, -r0, -r1, r0, 0};
-  double rr[3] = {r0, r1, r2};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      R.R_vote[3 * i + j] = (i == j ? 1.0 : 0.0) + s * K[3 * i + j] +
-                            c1 * (rr[i] * rr[j] - (i == j ? 1.0 : 0.0));
-}
+__device__ __noinline__ void kabsch_block(const InstDev& D, int a, int phase);
 
 // ---- FP64 sums of q p^T ----------------------------------------------------------------
 
@@ -481,8 +511,9 @@ struct PairQueues {
   }
 };
 
+// four blocks per SM: the once-per-instance Kabsch epilogue may spill, the pair loop does not
 template <int K>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     k_vote_set_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
   const StreamItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
@@ -521,12 +552,15 @@ __global__ void __launch_bounds__(kStreamThreads)
   }
   pq.flush(D, I.i0, lane);
   block_sums(pq.acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
+  // the last item of the instance solves the vote-set rotations
+  if (D.done && last_block(&D.done[2], (uint32_t)D.n_items))
+    for (int a = 0; a < kf; ++a) kabsch_block(D, a, 0);
 }
 
 // Residual labels against every R_init (float32 test of ||q - R p||^2 <= tau^2) and the
 // FP64 sums of each label class.
 template <int K>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     k_label_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
   const StreamItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
@@ -572,6 +606,9 @@ __global__ void __launch_bounds__(kStreamThreads)
   }
   pq.flush(D, I.i0, lane);
   block_sums(pq.acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
+  // the last item of the instance solves the refined rotations
+  if (D.done && last_block(&D.done[3], (uint32_t)D.n_items))
+    for (int a = 0; a < kf; ++a) kabsch_block(D, a, 1);
 }
 
 // ---- FP64 rotation from the sums (Horn's unit-quaternion method) --------------------------
@@ -816,19 +853,15 @@ __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
   return n2 < 2.5e-23f;
 }
 
-constexpr int kKabschThreads = 320;  // ten warps: one per summed quantity in the second stage
-
-// phase 0: R_init from the vote-set sums; phase 1: R from the label sums. One block per
-// (instance, rotation). The item partials are summed in a fixed order: thread t adds items
-// t, t + 320, ...; then warp j adds quantity j over the 320 threads. A dependent FP64
-// operation costs tens of cycles on this part, so the chains are kept short: the singularity
-// test needs no square root and X is M scaled by a power of two (the polar factor does not
-// depend on the scale).
-__global__ void __launch_bounds__(kKabschThreads) k_kabsch(const InstDev* __restrict__ insts, int max_k, int phase) {
-  const int inst = blockIdx.x / max_k, a = blockIdx.x % max_k;
-  const InstDev& D = insts[inst];
-  if (a >= *D.n_found) return;
-  __shared__ double part[kKabschThreads][10];
+// phase 0: R_init from the vote-set sums; phase 1: R from the label sums, for rotation a of
+// the instance. Called by a whole block (the last block of the sum kernel). The item partials
+// are summed in a fixed order: thread t adds items t, t + blockDim, ...; then each warp adds
+// some of the ten quantities over the threads; thread 0 solves for the rotation. A dependent
+// FP64 operation costs tens of cycles on this part, so the chains are kept short: the
+// singularity test needs no square root and X is M scaled by a power of two (the polar factor
+// does not depend on the scale).
+__device__ __noinline__ void kabsch_block(const InstDev& D, int a, int phase) {
+  __shared__ double part[kStreamThreads][10];
   __shared__ double tot[10];
   {
     double v[10];
@@ -838,59 +871,61 @@ __global__ void __launch_bounds__(kKabschThreads) k_kabsch(const InstDev* __rest
     for (int it = threadIdx.x; it < D.n_items; it += blockDim.x) {
       const double* src = base + (int64_t)it * D.k * 10;
 #pragma unroll
-      for (int t = 0; t < 10; ++t) v[t] += src[t];
+      for (int t = 0; t < 10; ++t) v[t] += __ldcg(src + t);
     }
 #pragma unroll
     for (int t = 0; t < 10; ++t) part[threadIdx.x][t] = v[t];
   }
   __syncthreads();
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (w < 10) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int col = w; col < 10; col += nw) {
     double v = 0.0;
-    for (int i = l; i < kKabschThreads; i += 32) v += part[i][w];
+    for (int i = l; i < (int)blockDim.x; i += 32) v += part[i][col];
     v = warp_sum_d(v);
-    if (l == 0) tot[w] = v;
+    if (l == 0) tot[col] = v;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double s[10];
+  if (threadIdx.x == 0) {
+    double s[10];
 #pragma unroll
-  for (int t = 0; t < 10; ++t) s[t] = tot[t];
-  DevRot& R = D.rot[a];
-  double out[9];
-  const uint32_t cnt = (uint32_t)s[9];
-  if (cnt == 0) {
-    const double* fb = phase == 0 ? R.R_vote : R.R_init;
-    for (int t = 0; t < 9; ++t) out[t] = fb[t];
-  } else {
-    // det M > 1e-9 |M|_F^3 (polar path) tested as det > 0 and det^2 > 1e-18 (|M|_F^2)^3
-    const double c0 = s[4] * s[8] - s[5] * s[7], c1 = s[5] * s[6] - s[3] * s[8], c2 = s[3] * s[7] - s[4] * s[6];
-    const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
-    const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
-                      (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
-    // X = M 2^-e with the largest |entry| in [1, 2) (exact)
-    double mx = 0.0;
-    for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
-    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
-    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
-    double X[9];
-    for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
-    double q[4];
-    const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
-                    polar_start_f32(X, q) && polar_refine_f64(X, q, out);
-    if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
-  }
-  if (phase == 0) {
-    for (int t = 0; t < 9; ++t) {
-      R.R_init[t] = out[t];
-      R.R_init_f[t] = (float)out[t];
+    for (int t = 0; t < 10; ++t) s[t] = tot[t];
+    DevRot& R = D.rot[a];
+    double out[9];
+    const uint32_t cnt = (uint32_t)s[9];
+    if (cnt == 0) {
+      const double* fb = phase == 0 ? R.R_vote : R.R_init;
+      for (int t = 0; t < 9; ++t) out[t] = fb[t];
+    } else {
+      // det M > 1e-9 |M|_F^3 (polar path) tested as det > 0 and det^2 > 1e-18 (|M|_F^2)^3
+      const double c0 = s[4] * s[8] - s[5] * s[7], c1 = s[5] * s[6] - s[3] * s[8], c2 = s[3] * s[7] - s[4] * s[6];
+      const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
+      const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
+                        (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
+      // X = M 2^-e with the largest |entry| in [1, 2) (exact)
+      double mx = 0.0;
+      for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
+      const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+      const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+      double X[9];
+      for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
+      double q[4];
+      const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
+                      polar_start_f32(X, q) && polar_refine_f64(X, q, out);
+      if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
     }
-    R.n_vote_set = cnt;
-  } else {
-    for (int t = 0; t < 9; ++t) R.R[t] = out[t];
-    R.n_inliers = cnt;
-    R.n_degenerate = *D.n_deg;
+    if (phase == 0) {
+      for (int t = 0; t < 9; ++t) {
+        R.R_init[t] = out[t];
+        R.R_init_f[t] = (float)out[t];
+      }
+      R.n_vote_set = cnt;
+    } else {
+      for (int t = 0; t < 9; ++t) R.R[t] = out[t];
+      R.n_inliers = cnt;
+      R.n_degenerate = *D.n_deg;
+    }
   }
+  __syncthreads();
 }
 
 // ---- least-squares axis of a set of pairs (Eq. 10) ---------------------------------------
@@ -1090,11 +1125,6 @@ void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts
   launches_add(1);
 }
 
-void launch_finalize_peaks(const InstDev* insts, int m, cudaStream_t st) {
-  k_finalize_peaks<<<(m + 127) / 128, 128, 0, st>>>(insts, m);
-  launches_add(1);
-}
-
 void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                        int max_J, cudaStream_t st) {
   size_t smem = (size_t)max_k * max_J * sizeof(uint32_t);
@@ -1104,11 +1134,6 @@ void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* inst
     attr = smem;
   }
   k_angle_vote<<<n_items, kStreamThreads, smem, st>>>(items, insts, max_J);
-  launches_add(1);
-}
-
-void launch_angle_peak(const InstDev* insts, int m, int max_k, cudaStream_t st) {
-  k_angle_peak<<<m * max_k, 256, 0, st>>>(insts, max_k);
   launches_add(1);
 }
 
@@ -1122,11 +1147,6 @@ void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* in
     k_vote_set_sum<4><<<n_items, kStreamThreads, 0, st>>>(items, insts);
   else
     k_vote_set_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
-  launches_add(1);
-}
-
-void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st) {
-  k_kabsch<<<m * max_k, kKabschThreads, 0, st>>>(insts, max_k, phase);
   launches_add(1);
 }
 

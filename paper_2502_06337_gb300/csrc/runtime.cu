@@ -138,7 +138,8 @@ struct InstPlan {
   int chunk, n_items, item0;
   // arena offsets
   size_t o_partial, o_grid, o_bins, o_msum, o_labels, o_vote_set, o_P, o_Q, o_mask;
-  size_t o_peak, o_hist, o_ndeg;   // zero region
+  size_t o_peak, o_hist, o_ndeg, o_done;  // zero region
+  int n_ritems = 0;
   size_t o_nfound, o_rot;          // result region
 };
 
@@ -366,8 +367,10 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     const int64_t red_words =
         m == 1 ? kReduceWords
                : kReduceWords * std::min<int64_t>(16, std::max<int64_t>(1, 64 / std::max(ip.S, 1)));
+    const size_t r0 = ritems.size();
     for (int64_t w0 = 0; w0 < words; w0 += red_words)
       ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + red_words, words)});
+    ip.n_ritems = (int)(ritems.size() - r0);
     ip.chunk = m == 1 ? stream_chunk(pb.n) : batch_chunk(total_n);
     ip.item0 = (int)sitems.size();
     for (int64_t a = 0; a < pb.n; a += ip.chunk)
@@ -401,6 +404,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     ip.o_peak = take(sizeof(unsigned long long) * ip.k);
     ip.o_hist = take(sizeof(uint32_t) * ip.k * ip.J);
     ip.o_ndeg = take(sizeof(uint32_t));
+    ip.o_done = take(sizeof(uint32_t) * 4);
   }
   const size_t zero_end = off;
   const size_t o_res = off;
@@ -459,6 +463,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     d.n_items = ip.n_items;
     d.n_found = reinterpret_cast<int32_t*>(D + ip.o_nfound);
     d.n_deg = reinterpret_cast<uint32_t*>(D + ip.o_ndeg);
+    d.done = reinterpret_cast<uint32_t*>(D + ip.o_done);
+    d.n_ritems = ip.n_ritems;
     d.rot = reinterpret_cast<DevRot*>(D + ip.o_rot);
     d.labels = (pb.labels && !pb.host_io) ? pb.labels : reinterpret_cast<int32_t*>(D + ip.o_labels);
     d.vote_set = pb.dbg ? pb.dbg->vote_set : nullptr;
@@ -508,15 +514,13 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
       vt->stop(st);
     else
       ok &= ck(cudaEventRecord(ws->tv1, st));
+    // each kernel's last block per instance finishes that instance's stage (peaks; angle peak
+    // and Rodrigues; the two Kabsch solves)
     launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
     for (int r = 1; r < max_k; ++r) launch_nms_round(drit, (int)ritems.size(), dinst, r, st);
-    launch_finalize_peaks(dinst, m, st);
     launch_angle_vote(dsit, (int)sitems.size(), dinst, max_k, max_J, st);
-    launch_angle_peak(dinst, m, max_k, st);
     launch_vote_set_sum(dsit, (int)sitems.size(), dinst, max_k, st);
-    launch_kabsch(dinst, m, max_k, 0, st);
     launch_label_sum(dsit, (int)sitems.size(), dinst, max_k, st);
-    launch_kabsch(dinst, m, max_k, 1, st);
     if (!ck(cudaGetLastError())) return false;
     ok &= ck(cudaMemcpyAsync(Hres, D + o_res, res_end - o_res, cudaMemcpyDeviceToHost, st));
     for (int i = 0; i < m; ++i) {

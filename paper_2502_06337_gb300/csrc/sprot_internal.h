@@ -55,6 +55,10 @@ struct InstDev {
   int32_t* labels;               // [n] (caller or workspace)
   uint8_t* vote_set;             // [k][n] or null
   uint8_t* mask;                 // [n] 1 = labelled inlier, or null
+  // per-stage arrival counters (zeroed per solve; null: no fused epilogues): [0] slice
+  // reduction and suppression rounds, [1] angle vote, [2] vote-set sums, [3] label sums
+  uint32_t* done;
+  int32_t n_ritems;              // this instance's slice-reduction items
 };
 
 struct VoteItem {
@@ -113,19 +117,18 @@ int launch_axis_vote_sampled(const float* P, const float* Q, int64_t n, int G, i
                              int n_sm, cudaStream_t st);
 void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
                            int grid_ctas, int tile_bytes, cudaStream_t st);
+// The slice reduction, suppression rounds, angle vote and FP64 sums finish each instance in the
+// last block to arrive (peaks, angle peak and Rodrigues, Kabsch) when InstDev::done is set.
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st);
 void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,
                       cudaStream_t st);
 void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, int32_t* n_found,
                         cudaStream_t st);
-void launch_finalize_peaks(const InstDev* insts, int m, cudaStream_t st);
 void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                        int max_J, cudaStream_t st);
-void launch_angle_peak(const InstDev* insts, int m, int max_k, cudaStream_t st);
 void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                          cudaStream_t st);
-void launch_kabsch(const InstDev* insts, int m, int max_k, int phase, cudaStream_t st);
 void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                       cudaStream_t st);
 double probe_smem_atomics(int iters, cudaStream_t st);
