@@ -1,11 +1,11 @@
 // Serving: continuous batching of independent rotation problems on one GPU.
 //
-// Requests queue on the host. Two worker threads, each owning a CUDA stream, a device input
+// Requests queue on the host. Worker threads, each owning a CUDA stream, a device input
 // arena and (through solve()) a device workspace, repeatedly take every request that fits
-// the device-memory budget from the front of the queue (admission), copy their inputs to the
-// device and solve them together with one launch sequence. While one worker's batch is on
-// the GPU the other admits the requests that arrived meanwhile and launches them on its own
-// stream, so consecutive batches overlap. Each request completes on its own (a waiter is
+// the device-memory budget from the front of the queue (admission; a batch holds at most
+// kServerBatchPairs pairs), copy their inputs to the device and solve them together with one
+// launch sequence. While one worker's batch is on the GPU another admits the requests that
+// arrived meanwhile and launches them on its own stream, so consecutive batches overlap. Each request completes on its own (a waiter is
 // woken per request), and its result depends only on its own inputs: instances share no
 // accumulator and no floating-point reduction.
 #include <chrono>
@@ -24,6 +24,12 @@ using namespace sprot;
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// Worker threads (each its own stream and workspace) and the pairs one batch may hold: small
+// batches and several in flight keep a request's wait short when large requests arrive in a
+// row, at loads well below the device's throughput.
+constexpr int kServerWorkers = 4;
+constexpr int64_t kServerBatchPairs = 2 << 20;
 
 struct Req {
   uint64_t ticket;
@@ -88,9 +94,12 @@ void sprot_server::worker_main(int idx) {
       });
       if (queue.empty()) break;  // stopping and drained
       double t = now_ms();
+      int64_t pairs = 0;
       while (!queue.empty() && (int)batch.size() < cfg.max_batch &&
-             in_use + queue.front()->bytes <= cfg.device_budget_bytes) {
+             in_use + queue.front()->bytes <= cfg.device_budget_bytes &&
+             (batch.empty() || pairs + queue.front()->r.n <= kServerBatchPairs)) {
         auto r = queue.front();
+        pairs += r->r.n;
         queue.pop_front();
         in_use += r->bytes;
         r->t_admit = t;
@@ -172,7 +181,7 @@ int sprot_server_create(const sprot_server_cfg* cfg, sprot_server** out) {
   if (s->cfg.max_batch <= 0) s->cfg.max_batch = 256;
   if (s->cfg.max_queue <= 0) s->cfg.max_queue = 65536;
   s->t0 = Clock::now();
-  for (int i = 0; i < 2; ++i) s->workers.emplace_back(&sprot_server::worker_main, s, i);
+  for (int i = 0; i < kServerWorkers; ++i) s->workers.emplace_back(&sprot_server::worker_main, s, i);
   *out = s;
   return SPROT_OK;
 }
