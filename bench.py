@@ -284,7 +284,7 @@ def run_sprot(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry, u32 votes, f64 refinement",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "dtype_detail": "f32 geometry, u32 vote counts, f64 least-squares refinement",
         "data": "synthetic (seeded; uniform cube points, uniform random rotation)",
         "config": {"workload": "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins",
                    "n": n, "grid": G, "angle_bins": J, "tau": tau, "parallelism": f"replicas x{world}",

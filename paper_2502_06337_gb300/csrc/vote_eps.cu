@@ -34,17 +34,19 @@ __device__ __forceinline__ void cols_meeting(float lo, float hi, float half, int
   b = (int)fminf(fmaxf(fb, -1.f), (float)(G - 1));
 }
 
-// Roots r1 <= r2 of c u^2 + 2 b u + k (c != 0, disc = b^2 - c k > 0), cancellation-free.
-__device__ __forceinline__ void roots2(float c, float b, float k, float disc, float& r1, float& r2) {
+// Roots r1 <= r2 of c u^2 + 2 b u + k (c != 0 with inv_c = 1/c, disc = b^2 - c k > 0),
+// cancellation-free; quotients by correctly rounded reciprocals.
+__device__ __forceinline__ void roots2(float inv_c, float b, float k, float disc, float& r1, float& r2) {
   const float q = -(b + copysignf(sqrtf(disc), b));
-  const float x = q / c, y = k / q;
+  const float x = q * inv_c, y = k * __frcp_rn(q);
   r1 = fminf(x, y);
   r2 = fmaxf(x, y);
 }
 
 // Column ranges of the cells meeting {u : sgn * (c u^2 + 2 b u + k) < 0} (sgn = +1 for S1,
 // -1 for S2).
-__device__ __forceinline__ Ranges cell_ranges(float c, float b, float k, float sgn, float half, int G) {
+__device__ __forceinline__ Ranges cell_ranges(float c, float inv_c, float b, float k, float sgn, float half,
+                                               int G) {
   Ranges R;
   R.n = 0;
   const float inf = __int_as_float(0x7f800000);
@@ -55,7 +57,7 @@ __device__ __forceinline__ Ranges cell_ranges(float c, float b, float k, float s
     const bool up = sgn * c > 0.f;  // sgn q opens upwards: negative between the roots
     if (disc > 0.f) {
       float r1, r2;
-      roots2(c, b, k, disc, r1, r2);
+      roots2(inv_c, b, k, disc, r1, r2);
       if (up) {
         lo0 = r1;
         hi0 = r2;
@@ -75,10 +77,10 @@ __device__ __forceinline__ Ranges cell_ranges(float c, float b, float k, float s
     const float bb = sgn * b, kk = sgn * k;
     if (bb > 0.f) {
       lo0 = -inf;
-      hi0 = -kk / (2.f * bb);
+      hi0 = -kk * __frcp_rn(2.f * bb);
       parts = 1;
     } else if (bb < 0.f) {
-      lo0 = -kk / (2.f * bb);
+      lo0 = -kk * __frcp_rn(2.f * bb);
       hi0 = inf;
       parts = 1;
     } else {
@@ -130,16 +132,15 @@ __device__ __forceinline__ void vote_span(uint32_t sbase, int W, int row, int a,
   if (c == b) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(1u) : "memory");
 }
 
-// min (lo) or max (!lo) of c v^2 + 2 b v over [v0, v1].
-__device__ __forceinline__ float quad_extreme(float c, float b, float v0, float v1, bool lo) {
-  const float f0 = v0 * fmaf(c, v0, 2.f * b), f1 = v1 * fmaf(c, v1, 2.f * b);
+// min (lo) or max (!lo) of c v^2 + 2 b v over [v0, v1] (inv_c = 1/c): the ends, and the
+// vertex value -b^2/c when the derivative 2 (c v + b) changes sign inside.
+__device__ __forceinline__ float quad_extreme(float c, float inv_c, float b, float v0, float v1, bool lo) {
+  const float s0 = fmaf(c, v0, b), s1 = fmaf(c, v1, b);
+  const float f0 = v0 * (s0 + b), f1 = v1 * (s1 + b);
   float r = lo ? fminf(f0, f1) : fmaxf(f0, f1);
-  if (c != 0.f) {
-    const float vs = -b / c;
-    if (vs > v0 && vs < v1) {
-      const float fv = -b * b / c;
-      r = lo ? fminf(r, fv) : fmaxf(r, fv);
-    }
+  if (c != 0.f && ((s0 < 0.f && s1 > 0.f) || (s0 > 0.f && s1 < 0.f))) {
+    const float fv = -b * b * inv_c;
+    r = lo ? fminf(r, fv) : fmaxf(r, fv);
   }
   return r;
 }
@@ -177,13 +178,14 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
       d3 = scalbnf(d3, -e);
       const float ed = eps * sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
       const float Cm = d3 - ed, Cp = d3 + ed;
+      const float iCm = Cm != 0.f ? __frcp_rn(Cm) : 0.f, iCp = Cp != 0.f ? __frcp_rn(Cp) : 0.f;
       for (int r = R0 + lane; r < R1; r += 32) {
         const float v0 = fmaf((float)r, step, -1.f), v1 = fmaf((float)(r + 1), step, -1.f);
         // F_minus = Cm (u^2 + v^2) + 2 d1 u + 2 d2 v - Cp ; F_plus = Cp (u^2 + v^2) + 2 d1 u + 2 d2 v - Cm
-        const float mr = quad_extreme(Cm, d2, v0, v1, true) - Cp;
-        const float Mr = quad_extreme(Cp, d2, v0, v1, false) - Cm;
-        const Ranges A = cell_ranges(Cm, d1, mr, 1.f, half, G);   // Cm u^2 + 2 d1 u + mr < 0
-        const Ranges B = cell_ranges(Cp, d1, Mr, -1.f, half, G);  // Cp u^2 + 2 d1 u + Mr > 0
+        const float mr = quad_extreme(Cm, iCm, d2, v0, v1, true) - Cp;
+        const float Mr = quad_extreme(Cp, iCp, d2, v0, v1, false) - Cm;
+        const Ranges A = cell_ranges(Cm, iCm, d1, mr, 1.f, half, G);   // Cm u^2 + 2 d1 u + mr < 0
+        const Ranges B = cell_ranges(Cp, iCp, d1, Mr, -1.f, half, G);  // Cp u^2 + 2 d1 u + Mr > 0
         for (int x = 0; x < A.n; ++x)
           for (int y = 0; y < B.n; ++y)
             vote_span(sbase, W, r - R0, max(A.a[x], B.a[y]), min(A.b[x], B.b[y]));
