@@ -1128,11 +1128,7 @@ void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts
 void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                        int max_J, cudaStream_t st) {
   size_t smem = (size_t)max_k * max_J * sizeof(uint32_t);
-  static size_t attr = 48 * 1024;
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_angle_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = smem;
-  }
+  if (smem > 48 * 1024) ensure_dynamic_smem(reinterpret_cast<const void*>(k_angle_vote), (int)smem);
   k_angle_vote<<<n_items, kStreamThreads, smem, st>>>(items, insts, max_J);
   launches_add(1);
 }

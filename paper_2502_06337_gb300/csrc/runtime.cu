@@ -24,6 +24,21 @@ namespace sprot {
 static std::atomic<uint64_t> g_launches{0};
 uint64_t launches_add(uint64_t k) { return g_launches.fetch_add(k) + k; }
 
+void ensure_dynamic_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  int& cur = done[{dev, func}];
+  if (bytes > cur) {
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+      cur = bytes;
+    else
+      cudaGetLastError();  // the launch reports the failure
+  }
+}
+
 // Axis-vote kernel timing (measurement only): events around each launch, read after the
 // launching call has synchronised its stream.
 static std::atomic<int> g_timing{0};

@@ -134,5 +134,9 @@ void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts
 double probe_smem_atomics(int iters, cudaStream_t st);
 
 uint64_t launches_add(uint64_t k);
+// Raises `func`'s dynamic shared-memory limit to at least `bytes` on the current device, once
+// per (device, function, size) and thread-safely (the launchers are called from several host
+// threads).
+void ensure_dynamic_smem(const void* func, int bytes);
 
 }  // namespace sprot

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
 
 void launch_axis_vote_eps(const VoteItem* items, int n_items, const InstDev* insts, int* counter, int grid_ctas,
                           int tile_bytes, float eps, cudaStream_t st) {
-  cudaFuncSetAttribute(k_axis_vote_eps, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes);
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_axis_vote_eps), tile_bytes);
   k_axis_vote_eps<<<grid_ctas, kEpsThreads, tile_bytes, st>>>(items, n_items, insts, counter, eps);
   launches_add(1);
 }

@@ -595,12 +595,7 @@ int vote_table_bytes() { return kWalkWarps * kTabWords * 4; }
 
 void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
                            int grid_ctas, int tile_bytes, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_axis_vote_walk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxSmemBytes);
-    attr = true;
-  }
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_axis_vote_walk), kMaxSmemBytes);
   k_axis_vote_walk<<<grid_ctas, kWalkThreads, tile_bytes + vote_table_bytes(), st>>>(
       items, n_items, insts, counter, tile_bytes / 4);
   launches_add(1);
