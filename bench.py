@@ -155,19 +155,17 @@ class ClockSampler:
 # the headline workload on the GPU
 # ---------------------------------------------------------------------------------------
 
-def vote_traffic():
-    """DRAM bytes (read + write) per launch of the axis-vote kernel from the committed ncu
-    capture, or None when the kernel source has changed since the counters were taken."""
+def vote_profile():
+    """The committed ncu record of the axis-vote kernel (DRAM bytes and warp instructions per
+    launch), or {} when the kernel source has changed since the counters were taken."""
     prof = os.path.join(ROOT, "profiles", "axis_vote_traffic.json")
     src = os.path.join(ROOT, "paper_2502_06337_gb300", "csrc", "vote_walk.cu")
     try:
         rec = json.load(open(prof))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
-        return None
-    if rec.get("kernel_source_sha256") != digest:
-        return None
-    return rec.get("dram_bytes_per_launch")
+        return {}
+    return rec if rec.get("kernel_source_sha256") == digest else {}
 
 
 def headline_problem(seed):
@@ -279,7 +277,17 @@ def run_sprot(args):
         "kernel_share_of_step": vote_s * 1e3 / (sum(step_ms) / len(step_ms)),
         "traffic": None,
     }
-    roofline["traffic"] = vote_traffic()
+    rec = vote_profile()
+    roofline["traffic"] = rec.get("dram_bytes_per_launch")
+    # instruction issue, the kernel's binding limit: warp instructions per launch (committed
+    # capture of the same source) over the live kernel time, against 4 issue slots per SM per
+    # cycle at the SM clock sampled during the timed region
+    if rec.get("warp_instructions_per_launch") and clocks.get("sm_mhz"):
+        slots = rec["grid_ctas"] * 4 * clocks["sm_mhz"] * 1e6
+        roofline["issue"] = {"achieved_warp_inst_per_s": rec["warp_instructions_per_launch"] / vote_s,
+                             "peak_warp_inst_per_s": slots, "unit": "warp instructions/s",
+                             "frac": rec["warp_instructions_per_launch"] / vote_s / slots,
+                             "note": "SMs the grid occupies x 4 schedulers x measured SM clock"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
