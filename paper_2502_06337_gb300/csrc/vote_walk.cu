@@ -41,13 +41,16 @@ __device__ __forceinline__ float edgef(int k, float step) { return fmaf((float)k
 
 // Roots lo <= hi of c3 y^2 + 2 b y + kk = 0 (c3 >= 0, inv3 = 1/c3, +inf for c3 = 0), one from
 // |b| + sqrt(disc) and the other from the product of the roots. Returns false (roots NaN)
-// when the quadratic has no real root.
+// when the quadratic has no real root. The square root and quotient are the hardware
+// approximations (a few ulp): a root only places a start cell or a piece boundary, and a
+// start cell is wrong only when the root lies within rounding of a cell edge, where F at that
+// edge is within the boundary band.
 __device__ __forceinline__ bool qroots(float c3, float inv3, float b, float kk, float& lo,
                                        float& hi) {
   const float disc = fmaf(-c3, kk, b * b);
-  const float t = fabsf(b) + sqrtf(disc);
+  const float t = fabsf(b) + (disc > 0.f ? disc * rsqrtf(disc) : sqrtf(disc));
   const float far = t * inv3;
-  const float nr = t > 0.f ? kk * __frcp_rn(t) : 0.f;  // t = 0: b = 0, double root at 0
+  const float nr = t > 0.f ? __fdividef(kk, t) : 0.f;  // t = 0: b = 0, double root at 0
   lo = b >= 0.f ? -far : nr;
   hi = b >= 0.f ? -nr : far;
   return disc >= 0.f;
@@ -125,8 +128,8 @@ __device__ void prepare(const Band& B, float d1, float d2, float d3, Prepared& S
   const float s = 0.70710678f;
   // 45-degree points cx -/+ rho/sqrt(2), without cancellation
   const float q1 = fmaf(d2, d2, d3 * d3) - d1 * d1;
-  const float uA = d1 >= 0.f ? -(d1 + s * nd) * inv3 : -0.5f * q1 / ((s * nd - d1) * d3);
-  const float uB = d1 <= 0.f ? (s * nd - d1) * inv3 : 0.5f * q1 / ((s * nd + d1) * d3);
+  const float uA = d1 >= 0.f ? -(d1 + s * nd) * inv3 : __fdividef(-0.5f * q1, (s * nd - d1) * d3);
+  const float uB = d1 <= 0.f ? (s * nd - d1) * inv3 : __fdividef(0.5f * q1, (s * nd + d1) * d3);
   const int jA = min(max(cell_clamped(uA, B.half, -2, G + 2), -1), G - 1);
   const int jB = min(max(cell_clamped(uB, B.half, -2, G + 2), 0), G);
   S.jAB = (uint32_t)(jA + 1) | ((uint32_t)jB << 16);
