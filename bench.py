@@ -500,9 +500,10 @@ def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40):
         probs.append((pb, B.make_params(grid=0, angle_bins=360, k=k, nms_deg=2.0, tau=synth.default_tau(0.01))))
     srv = B.Server(budget_gb << 30, max_batch=256)
     try:
-        # warm-up
-        for pb, prm in probs[:4]:
-            srv.wait(srv.submit(pb.P, pb.Q, prm))
+        # warm-up: every pool problem once, all in flight (sizes the workers' arenas and
+        # workspaces before timing)
+        for t in [srv.submit(pb.P, pb.Q, prm) for pb, prm in probs]:
+            srv.wait(t)
         tickets = []
         t0 = time.perf_counter()
         for i, s in enumerate(specs):

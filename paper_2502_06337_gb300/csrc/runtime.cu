@@ -170,6 +170,7 @@ struct GraphEntry {
 struct Workspace {
   std::mutex mu;
   int device = 0;
+  cudaStream_t stream = nullptr;  // the stream the workspace serves (allocations are ordered on it)
   char* dev = nullptr;
   size_t dev_cap = 0;
   char* host = nullptr;  // pinned
@@ -197,25 +198,36 @@ struct Workspace {
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
+  // Device memory grows geometrically and is allocated and freed in stream order
+  // (cudaMallocAsync / cudaFreeAsync): a synchronous cudaFree would wait for the whole device,
+  // stalling the other workspaces' streams (e.g. concurrent server batches).
   int reserve(size_t dbytes, size_t hbytes) {
     if (dbytes > dev_cap || hbytes > host_cap) drop_graphs();  // their addresses are about to change
     if (dbytes > dev_cap) {
       size_t want = std::max(dbytes, dev_cap + dev_cap / 2);
-      if (dev) cudaFree(dev);
+      if (dev && cudaFreeAsync(dev, stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dev);
+      }
       dev = nullptr;
       dev_cap = 0;
-      if (cudaMalloc(&dev, want) != cudaSuccess) {
+      auto alloc = [&](size_t b) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&dev), b, stream) == cudaSuccess) return true;
         cudaGetLastError();
-        if (cudaMalloc(&dev, dbytes) != cudaSuccess) {
-          cudaGetLastError();
-          dev = nullptr;
-          return SPROT_E_NOMEM;
-        }
+        dev = nullptr;
+        if (cudaMalloc(&dev, b) == cudaSuccess) return true;
+        cudaGetLastError();
+        dev = nullptr;
+        return false;
+      };
+      if (!alloc(want)) {
+        if (!alloc(dbytes)) return SPROT_E_NOMEM;
         want = dbytes;
       }
       dev_cap = want;
     }
     if (hbytes > host_cap) {
+      hbytes = std::max<size_t>(hbytes, std::max<size_t>(4u << 20, host_cap * 2));  // rare regrowth
       if (host) cudaFreeHost(host);
       host = nullptr;
       host_cap = 0;
@@ -244,6 +256,7 @@ Workspace* workspace_for(cudaStream_t st, int* status) {
   if (!slot) {
     slot.reset(new Workspace());
     slot->device = dev;
+    slot->stream = st;
   }
   *status = SPROT_OK;
   return slot.get();

@@ -30,6 +30,8 @@ using Clock = std::chrono::steady_clock;
 // row, at loads well below the device's throughput.
 constexpr int kServerWorkers = 4;
 constexpr int64_t kServerBatchPairs = 2 << 20;
+// initial input arena of a worker: a full batch of pairs (P and Q, 12 bytes each per pair)
+constexpr size_t kServerArenaBytes = (size_t)kServerBatchPairs * 24 + (64u << 10);
 
 struct Req {
   uint64_t ticket;
@@ -106,18 +108,24 @@ void sprot_server::worker_main(int idx) {
         batch.push_back(r);
       }
     }
-    // inputs -> device arena
+    // inputs -> device arena (grown geometrically, in stream order: a synchronous free would
+    // wait for the other workers' batches)
     size_t need = 0;
     for (auto& r : batch) need += ((size_t)r->r.n * 12 + 255) / 256 * 256 * 2;
     int status = SPROT_OK;
     if (need > arena_cap) {
-      if (arena) cudaFree(arena);
+      const size_t want = std::max(need, std::max<size_t>(arena_cap * 2, kServerArenaBytes));
+      if (arena && cudaFreeAsync(arena, st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(arena);
+      }
       arena = nullptr;
       arena_cap = 0;
-      if (cudaMalloc(&arena, need) == cudaSuccess)
-        arena_cap = need;
-      else {
+      if (cudaMallocAsync(reinterpret_cast<void**>(&arena), want, st) == cudaSuccess) {
+        arena_cap = want;
+      } else {
         cudaGetLastError();
+        arena = nullptr;
         status = SPROT_E_NOMEM;
       }
     }
@@ -164,7 +172,8 @@ void sprot_server::worker_main(int idx) {
     cv_done.notify_all();
     cv_work.notify_all();
   }
-  if (arena) cudaFree(arena);
+  if (arena) cudaFreeAsync(arena, st);
+  cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
 }
 
