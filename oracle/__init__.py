@@ -27,6 +27,8 @@ from .vote import (  # noqa: F401
     BAND,
     grid_edges,
     cell_axis,
+    subcell_offset,
+    subcell_axis,
     circle_cell_extrema,
     axis_vote,
     cell_votes,

@@ -195,6 +195,43 @@ def top_k_cells(grid, k: int, nms_deg: float):
     return peaks
 
 
+def subcell_offset(grid, row: int, col: int):
+    """Sub-cell position of a peak, in cells, along u (columns) and v (rows).
+
+    Algorithm 1 back-projects the centre of the peak cell (Eq. 12), so the axis carries up
+    to half a cell of quantisation. Reading (the paper gives no interpolation): along each
+    grid axis a parabola is fitted through the counts of the peak cell and its two edge
+    neighbours, c(-1), c(0), c(1), and the peak is placed at its vertex,
+        delta = (c(-1) - c(1)) / (2 (c(-1) - 2 c(0) + c(1))),
+    clamped to [-1/2, 1/2] (the cell itself). The offset along an axis is 0 when the
+    parabola does not open downwards (c(-1) - 2 c(0) + c(1) >= 0) or when the peak lies on
+    the grid border along that axis (a neighbour is missing). Returns (du, dv)."""
+    grid = np.asarray(grid)
+    G = grid.shape[1]
+    c0 = float(grid[row, col])
+
+    def vertex(cm, cp):
+        den = float(cm) - 2.0 * c0 + float(cp)
+        if den >= 0.0:
+            return 0.0
+        return min(0.5, max(-0.5, 0.5 * (float(cm) - float(cp)) / den))
+
+    du = vertex(grid[row, col - 1], grid[row, col + 1]) if 0 < col < G - 1 else 0.0
+    dv = vertex(grid[row - 1, col], grid[row + 1, col]) if 0 < row < G - 1 else 0.0
+    return du, dv
+
+
+def subcell_axis(G: int, row: int, col: int, du: float, dv: float) -> np.ndarray:
+    """The axis at the sub-cell point (centre of cell (row, col) moved by du, dv cells),
+    back-projected by Eq. 12 and canonicalised to r_z <= 0 like ``cell_axis``."""
+    u = -1.0 + (2.0 * col + 1.0 + 2.0 * du) / G
+    v = -1.0 + (2.0 * row + 1.0 + 2.0 * dv) / G
+    r = inverse_stereographic_projection(u, v)
+    if r[2] > 0:
+        r = -r
+    return r
+
+
 # ---------------------------------------------------------------------------------------
 # Angle vote (Algorithm 1 second loop; Sec. IV-B, Eq. 15)
 # ---------------------------------------------------------------------------------------
@@ -570,7 +607,7 @@ def sampled_axis_vote(P, Q, G: int, J: int):
 # ---------------------------------------------------------------------------------------
 
 def solve(P, Q, G: int, J: int, k: int = 1, nms_deg: float = 2.0, w: int = 1,
-          window: int = 1, tau: float = 0.05, grid=None):
+          window: int = 1, tau: float = 0.05, grid=None, subcell: bool = False):
     """Algorithm 1 end to end, plus the multi-rotation form (Sec. IV-D) and refinement.
 
     For each of up to k peaks: axis r (Eq. 12 at the cell centre, r_z <= 0), gate, angle
@@ -578,6 +615,9 @@ def solve(P, Q, G: int, J: int, k: int = 1, nms_deg: float = 2.0, w: int = 1,
     replaced by (-r, -theta) so that theta lies in [0, pi] as in Sec. III-A; R_vote by
     Rodrigues (Eq. 2); vote set V; R1 = Kabsch(V). Then labels against every R1 and
     R = Kabsch over each label class.
+
+    With ``subcell`` the axis of each peak is ``subcell_axis`` at ``subcell_offset`` instead
+    of the cell centre (the gate still uses the peak's cells).
 
     ``grid`` may be passed in (e.g. a float32 implementation's grid) to evaluate the later
     stages on it. Returns a dict with every intermediate."""
@@ -592,7 +632,8 @@ def solve(P, Q, G: int, J: int, k: int = 1, nms_deg: float = 2.0, w: int = 1,
     out["peaks"] = peaks
     rots = []
     for (row, col, cnt) in peaks:
-        r = cell_axis(G, row, col)
+        du, dv = subcell_offset(grid, row, col)
+        r = subcell_axis(G, row, col, du, dv) if subcell else cell_axis(G, row, col)
         gate, gflag = window_gate(P, Q, G, row, col, w)
         vote = angle_vote(P, Q, r, gate, gflag, J)
         b, th = angle_peak(vote["hist"])
@@ -601,6 +642,7 @@ def solve(P, Q, G: int, J: int, k: int = 1, nms_deg: float = 2.0, w: int = 1,
         R_vote = rodrigues(axis, theta)
         R1 = kabsch(P[V], Q[V]) if V.any() else R_vote
         rots.append(dict(cell=(row, col), axis_votes=cnt, axis=axis, r_cell=r, theta=theta,
+                         cell_offset=(du, dv),
                          bin=b, angle_votes=int(vote["hist"][b]), R_vote=R_vote, gate=gate,
                          gate_flag=gflag, vote=vote, V=V, V_lo=V_lo, V_hi=V_hi, R1=R1))
     labels, lflag = assign_labels(P, Q, [x["R1"] for x in rots], tau)

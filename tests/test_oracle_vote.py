@@ -522,3 +522,81 @@ def test_eps_band_tiny_eps_is_the_curve_test():
     curve = oracle.axis_vote(prob.P, prob.Q, G)
     both = (band["lo"] == band["hi"]) & (curve["lo"] == curve["hi"])
     assert np.array_equal(band["grid"][both], curve["grid"][both]) and both.mean() > 0.99
+
+
+# ---- sub-cell peak (three-point parabola per grid axis) --------------------------------------
+
+def test_subcell_offset_recovers_a_separable_parabola():
+    """f(u, v) = 1010 - 16 (u - 1/4)^2 - 64 (v + 3/8)^2 sampled at the peak cell and its edge
+    neighbours gives the integers c0 = 1000, (976, 992) along u and (984, 888) along v; a
+    parabola through three samples of a parabola is that parabola, so the vertex is
+    (1/4, -3/8) exactly."""
+    g = np.zeros((5, 5), dtype=np.int64)
+    g[2, 2] = 1000
+    g[2, 1], g[2, 3] = 976, 992
+    g[1, 2], g[3, 2] = 984, 888
+    assert ov.subcell_offset(g, 2, 2) == (0.25, -0.375)
+
+
+def test_subcell_offset_matches_polyfit_vertex():
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        c0 = int(rng.integers(10, 1000))
+        cm, cp = (int(x) for x in rng.integers(0, c0, 2))
+        g = np.zeros((3, 3), dtype=np.int64)
+        g[1, 1], g[1, 0], g[1, 2] = c0, cm, cp
+        g[0, 1], g[2, 1] = cp, cm  # the v axis sees the same triple mirrored
+        a, b, _ = np.polyfit([-1.0, 0.0, 1.0], [cm, c0, cp], 2)
+        want = float(np.clip(-b / (2.0 * a), -0.5, 0.5))
+        du, dv = ov.subcell_offset(g, 1, 1)
+        assert abs(du - want) < 1e-12 and abs(dv + want) < 1e-12
+
+
+def test_subcell_offset_special_cases():
+    g = np.zeros((4, 4), dtype=np.int64)
+    g[1, 1] = 10
+    g[1, 0] = g[1, 2] = 6  # symmetric along u
+    g[0, 1] = 10           # flat towards v = -1: vertex on the cell edge
+    assert ov.subcell_offset(g, 1, 1) == (0.0, -0.5)
+    g[0, 1] = 12           # a larger neighbour (an NMS peak next to a suppressed cell): clamped
+    assert ov.subcell_offset(g, 1, 1)[1] == -0.5
+    f = np.full((4, 4), 3, dtype=np.int64)
+    assert ov.subcell_offset(f, 1, 2) == (0.0, 0.0)  # flat: no downward parabola
+    b = np.zeros((4, 4), dtype=np.int64)
+    b[0, 3], b[0, 2], b[1, 3] = 9, 5, 1
+    assert ov.subcell_offset(b, 0, 3) == (0.0, 0.0)  # corner cell: a neighbour is missing on both axes
+
+
+def test_subcell_axis_edges_and_centre():
+    """Zero offset is the cell-centre axis; half a cell towards a neighbour is the midpoint
+    of the shared edge, reached from either cell."""
+    G = 32
+    for row, col in [(3, 7), (16, 16), (30, 1)]:
+        assert np.allclose(ov.subcell_axis(G, row, col, 0.0, 0.0), ov.cell_axis(G, row, col), atol=1e-15)
+        assert np.allclose(ov.subcell_axis(G, row, col, 0.5, 0.0), ov.subcell_axis(G, row, col + 1, -0.5, 0.0),
+                           atol=1e-15)
+        assert np.allclose(ov.subcell_axis(G, row, col, 0.0, -0.5), ov.subcell_axis(G, row - 1, col, 0.0, 0.5),
+                           atol=1e-15)
+        r = ov.subcell_axis(G, row, col, 0.3, -0.2)
+        assert abs(np.linalg.norm(r) - 1.0) < 1e-15 and r[2] <= 0.0
+
+
+def test_subcell_axis_is_closer_to_the_true_axis():
+    """Noise-free problems with outliers: over many random rotations the sub-cell axis lies
+    closer to the true axis than the peak cell's centre (a wrong sign or axis would move it
+    away)."""
+    G = 64
+    centre, sub, better = [], [], 0
+    for seed in range(16):
+        prob = synth.make_problem(3000, (0.5,), 0.0, seed=100 + seed)
+        out = ov.solve(prob.P, prob.Q, G, 360, subcell=True)
+        row, col = out["peaks"][0][:2]
+        rv = Rotation.from_matrix(prob.rotations[0]).as_rotvec()
+        r_true = rv / np.linalg.norm(rv)
+        e0 = ov.axis_angle_deg(ov.cell_axis(G, row, col), r_true)
+        e1 = ov.axis_angle_deg(out["rotations"][0]["r_cell"], r_true)
+        centre.append(e0)
+        sub.append(e1)
+        better += e1 < e0
+    assert np.mean(sub) < 0.6 * np.mean(centre)
+    assert better >= 12
