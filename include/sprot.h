@@ -55,6 +55,13 @@ extern "C" {
 
 /* ---- flags ------------------------------------------------------------------------------ */
 #define SPROT_HOST_PTRS 0x1u /* P, Q and per-pair outputs are host pointers */
+/* The axis of each peak is taken at its sub-cell position instead of the cell centre: along
+ * each grid axis, the vertex of the parabola through the counts of the peak cell and its two
+ * edge neighbours, clamped to the cell (offset 0 where the parabola does not open downwards
+ * or a neighbour is off the grid). The angle vote, R_vote and the reported axis use it; the
+ * gate still uses the peak's cells. The paper back-projects the cell centre (Algorithm 1,
+ * Eq. 12); the offsets are reported in sprot_rotation.cell_offset with or without the flag. */
+#define SPROT_SUBCELL_AXIS 0x2u
 
 /* ---- limits ----------------------------------------------------------------------------- */
 #define SPROT_MAX_K 8          /* rotations per problem */
@@ -77,7 +84,7 @@ typedef struct sprot_params {
                            (circularly). Default 1. */
   double tau;           /* inlier residual threshold ||q - R p|| <= tau: the "noise level"
                            input of Algorithm 1 (default 0.05) */
-  uint32_t flags;       /* SPROT_HOST_PTRS */
+  uint32_t flags;       /* SPROT_HOST_PTRS | SPROT_SUBCELL_AXIS; other bits: E_INVAL */
 } sprot_params;
 
 /* One estimated rotation. Axis/angle/R_vote are the paper's estimate (Sec. IV-C); R_init and
@@ -87,7 +94,8 @@ typedef struct sprot_rotation {
   double R[9];          /* refined rotation, row-major */
   double R_init[9];     /* Kabsch over the angle-vote set */
   double R_vote[9];     /* Rodrigues(axis, theta) */
-  double axis[3];       /* unit axis (cell centre by Eq. 12), sign chosen so theta in [0,pi] */
+  double axis[3];       /* unit axis (cell centre by Eq. 12, or the sub-cell point with
+                           SPROT_SUBCELL_AXIS), sign chosen so theta in [0,pi] */
   double theta;         /* bin-centre angle, radians, in [0, pi] */
   int32_t cell_row, cell_col; /* peak cell */
   int32_t angle_bin;    /* peak bin of the histogram about the canonical (r_z <= 0) axis */
@@ -96,6 +104,8 @@ typedef struct sprot_rotation {
   uint32_t n_vote_set;  /* pairs in the angle-vote set used for R_init */
   uint32_t n_inliers;   /* pairs labelled with this rotation */
   uint32_t n_degenerate;/* pairs with p_i == q_i exactly (no circle) */
+  double cell_offset[2]; /* sub-cell peak position relative to the cell centre, in cells,
+                           along u (columns) and v (rows); each in [-1/2, 1/2] */
 } sprot_rotation;
 
 /* Fills the defaults listed in sprot_params. */

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libsprot.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOAXIS, E_UNIMPL, E_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
 HOST_PTRS = 0x1
+SUBCELL_AXIS = 0x2
 MAX_K = 8
 
 EXPORTS = [
@@ -41,7 +42,7 @@ class Rotation(C.Structure):
                 ("axis", C.c_double * 3), ("theta", C.c_double), ("cell_row", C.c_int32),
                 ("cell_col", C.c_int32), ("angle_bin", C.c_int32), ("axis_votes", C.c_uint32),
                 ("angle_votes", C.c_uint32), ("n_vote_set", C.c_uint32), ("n_inliers", C.c_uint32),
-                ("n_degenerate", C.c_uint32)]
+                ("n_degenerate", C.c_uint32), ("cell_offset", C.c_double * 2)]
 
     def to_dict(self) -> dict:
         return dict(
@@ -50,7 +51,8 @@ class Rotation(C.Structure):
             theta=float(self.theta), cell=(int(self.cell_row), int(self.cell_col)),
             bin=int(self.angle_bin), axis_votes=int(self.axis_votes),
             angle_votes=int(self.angle_votes), n_vote_set=int(self.n_vote_set),
-            n_inliers=int(self.n_inliers), n_degenerate=int(self.n_degenerate))
+            n_inliers=int(self.n_inliers), n_degenerate=int(self.n_degenerate),
+            cell_offset=(float(self.cell_offset[0]), float(self.cell_offset[1])))
 
 
 class Debug(C.Structure):
@@ -288,6 +290,8 @@ def _rotation_dtype():
                 f.append((name, ("<f8", (9,)), off))
             elif name == "axis":
                 f.append((name, ("<f8", (3,)), off))
+            elif name == "cell_offset":
+                f.append((name, ("<f8", (2,)), off))
             else:
                 f.append((name, {C.c_double: "<f8", C.c_int32: "<i4", C.c_uint32: "<u4"}[t], off))
         _ROTATION_DTYPE = np.dtype({"names": [x[0] for x in f], "formats": [x[1] for x in f],
@@ -315,7 +319,8 @@ class BatchResult:
                             theta=float(r["theta"]), cell=(int(r["cell_row"]), int(r["cell_col"])),
                             bin=int(r["angle_bin"]), axis_votes=int(r["axis_votes"]),
                             angle_votes=int(r["angle_votes"]), n_vote_set=int(r["n_vote_set"]),
-                            n_inliers=int(r["n_inliers"]), n_degenerate=int(r["n_degenerate"])))
+                            n_inliers=int(r["n_inliers"]), n_degenerate=int(r["n_degenerate"]),
+                            cell_offset=(float(r["cell_offset"][0]), float(r["cell_offset"][1]))))
         return out
 
     def __getitem__(self, i):

@@ -46,14 +46,27 @@ __device__ unsigned long long block_max_u64(unsigned long long v) {
 struct CellAxis {
   double w0, w1, w2, N;
 };
-__device__ __forceinline__ CellAxis cell_axis(int G, int row, int col) {
-  double a = 2.0 * col + 1.0 - G, b = 2.0 * row + 1.0 - G, g = (double)G;
+// Eq. 12 at the plane point (a, b) / G, unnormalised: w / N is the unit axis.
+__device__ __forceinline__ CellAxis axis_at(double a, double b, double g) {
   CellAxis c;
   c.w0 = 2.0 * a * g;
   c.w1 = 2.0 * b * g;
   c.w2 = a * a + b * b - g * g;
   c.N = g * g + a * a + b * b;
   return c;
+}
+// The axis of a cell's centre (u, v) = ((2 col + 1 - G) / G, (2 row + 1 - G) / G).
+__device__ __forceinline__ CellAxis cell_axis(int G, int row, int col) {
+  return axis_at(2.0 * col + 1.0 - G, 2.0 * row + 1.0 - G, (double)G);
+}
+
+// Sub-cell peak along one grid axis: the vertex of the parabola through the counts cm, c0, cp
+// at offsets -1, 0, +1, i.e. (cm - cp) / (2 (cm - 2 c0 + cp)), clamped to the cell; 0 when the
+// parabola does not open downwards. Integer counts make every step but the quotient exact.
+__device__ __forceinline__ double parabola_vertex(uint32_t cm, uint32_t c0, uint32_t cp) {
+  const double den = (double)cm - 2.0 * (double)c0 + (double)cp;
+  if (!(den < 0.0)) return 0.0;
+  return fmin(0.5, fmax(-0.5, 0.5 * ((double)cm - (double)cp) / den));
 }
 
 // Axis lines of two cells within the suppression radius: |r1 . r2| >= cos(radius).
@@ -88,9 +101,17 @@ __device__ void finalize_instance(const InstDev& D) {
     const unsigned long long key = __ldcg(D.peak_key + a);
     if (!key) break;
     const uint32_t idx = 0xffffffffu - (uint32_t)(key & 0xffffffffu);
-    const int row = idx / D.G, col = idx % D.G;
+    const int G = D.G, row = idx / G, col = idx % G;
     DevRot& R = D.rot[a];
-    const CellAxis c = cell_axis(D.G, row, col);
+    // sub-cell offsets from the edge neighbours (none along an axis at the grid border)
+    const uint32_t c0 = (uint32_t)(key >> 32);
+    const uint32_t* g = D.grid + (int64_t)row * G + col;
+    const double du = (col > 0 && col < G - 1) ? parabola_vertex(__ldcg(g - 1), c0, __ldcg(g + 1)) : 0.0;
+    const double dv = (row > 0 && row < G - 1) ? parabola_vertex(__ldcg(g - G), c0, __ldcg(g + G)) : 0.0;
+    R.cell_offset[0] = du;
+    R.cell_offset[1] = dv;
+    const CellAxis c = D.subcell ? axis_at(2.0 * col + 1.0 + 2.0 * du - G, 2.0 * row + 1.0 + 2.0 * dv - G, (double)G)
+                                 : cell_axis(G, row, col);
     const double sgn = c.w2 > 0 ? -1.0 : 1.0;  // canonical: southern hemisphere, r_z <= 0
     const double r0 = sgn * c.w0 / c.N, r1 = sgn * c.w1 / c.N, r2 = sgn * c.w2 / c.N;
     R.axis[0] = r0;

@@ -105,6 +105,7 @@ int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, i
   if (!(p->tau > 0.0) || !std::isfinite(p->tau)) return SPROT_E_INVAL;
   if (!(p->nms_deg >= 0.f) || !std::isfinite(p->nms_deg)) return SPROT_E_INVAL;
   if (p->gate_window < -1 || p->angle_window < 0) return SPROT_E_INVAL;
+  if (p->flags & ~(SPROT_HOST_PTRS | SPROT_SUBCELL_AXIS)) return SPROT_E_INVAL;
   return SPROT_OK;
 }
 
@@ -478,6 +479,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     d.window = ip.window;
     d.n_bands = ip.T;
     d.S = ip.S;
+    d.subcell = (pb.prm.flags & SPROT_SUBCELL_AXIS) ? 1 : 0;
     d.tau = ip.tau;
     d.cos_nms = ip.cos_nms;
     for (int b = 0; b <= ip.T; ++b) d.band_row0[b] = ip.row0[b];
@@ -606,6 +608,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
       o.n_vote_set = r.n_vote_set;
       o.n_inliers = r.n_inliers;
       o.n_degenerate = r.n_degenerate;
+      o.cell_offset[0] = r.cell_offset[0];
+      o.cell_offset[1] = r.cell_offset[1];
     }
     if (nf == 0) worst = SPROT_E_NOAXIS;
     probs[i].prm.grid = ip.G;

@@ -29,6 +29,7 @@ struct DevRot {
   float R_init_f[9]; // R_init rounded to float32, used by the residual labels
   int32_t cell_row, cell_col, angle_bin;
   uint32_t axis_votes, angle_votes, n_vote_set, n_inliers, n_degenerate;
+  double cell_offset[2];  // sub-cell peak offset (u, v) in cells
 };
 
 // One problem of a (possibly single-element) batch, as the kernels see it.
@@ -38,6 +39,7 @@ struct InstDev {
   int64_t n;
   int32_t G, J, k, w, window;
   int32_t n_bands, S;            // row bands and circle slices of the axis vote
+  int32_t subcell;               // axis at the sub-cell peak (SPROT_SUBCELL_AXIS)
   float tau;
   double cos_nms;                // cosine of the suppression radius between axis lines
   int32_t band_row0[kMaxBands + 1];

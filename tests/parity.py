@@ -40,7 +40,7 @@ def check_lsq(P_sel, Q_sel, R_gpu, R_fallback):
         assert abs(np.trace(R_gpu.T @ M) - best) <= 1e-12 * max(1.0, s[0])
 
 
-def run_gpu(P, Q, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, host=False):
+def run_gpu(P, Q, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, host=False, subcell=False):
     """The CUDA solve with every intermediate exported. Returns a dict of numpy arrays."""
     import torch
 
@@ -57,7 +57,8 @@ def run_gpu(P, Q, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, host=False):
         vote_set=torch.zeros(k * n, dtype=torch.uint8, device=dev),
     )
     labels = torch.zeros(n, dtype=torch.int32, device=dev)
-    prm = B.make_params(grid=G, angle_bins=J, k=k, nms_deg=nms, gate_window=w, angle_window=window, tau=tau)
+    prm = B.make_params(grid=G, angle_bins=J, k=k, nms_deg=nms, gate_window=w, angle_window=window, tau=tau,
+                        flags=B.SUBCELL_AXIS if subcell else 0)
     rots = B.estimate_rotations(Pt, Qt, prm, labels=labels, debug=dbg, allow_noaxis=True)
     torch.cuda.synchronize()
     u32 = lambda t: t.cpu().numpy().view(np.uint32).astype(np.int64)
@@ -82,9 +83,10 @@ def check_grid(gpu_grid, av, what=""):
     return int((~certain).sum())
 
 
-def check_solve(P, Q, g, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, av=None):
+def check_solve(P, Q, g, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, av=None, subcell=False):
     """Every stage of one GPU solve ``g`` (from run_gpu) against the oracle. ``av`` may hold a
-    precomputed oracle axis vote. Returns a dict of flagged counts."""
+    precomputed oracle axis vote; ``subcell``: the solve used the sub-cell axis. Returns a dict
+    of flagged counts."""
     P = np.asarray(P, dtype=np.float32)
     Q = np.asarray(Q, dtype=np.float32)
     report = {}
@@ -96,7 +98,10 @@ def check_solve(P, Q, g, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, av=None):
     R1s = []
     for a, rot in enumerate(g["rots"]):
         row, col = rot["cell"]
-        r = oracle.cell_axis(G, row, col)
+        # sub-cell offsets: exact integer arithmetic and one quotient on both sides
+        off = oracle.subcell_offset(g["grid"], row, col)
+        assert rot["cell_offset"] == off, (rot["cell_offset"], off)
+        r = oracle.subcell_axis(G, row, col, *off) if subcell else oracle.cell_axis(G, row, col)
         gate, gflag = oracle.window_gate(P, Q, G, row, col, w)
         av_ = oracle.angle_vote(P, Q, r, gate, gflag, J)
         hist = g["hist"][a]
@@ -108,7 +113,7 @@ def check_solve(P, Q, g, G, J, k=1, nms=2.0, w=1, window=1, tau=0.05, av=None):
         assert rot["bin"] == b and rot["angle_votes"] == int(hist[b])
         # axis and R_vote are exact functions of (cell, bin)
         axis, theta = (r, th) if th >= 0 else (-r, -th)
-        assert np.allclose(rot["axis"], axis, atol=1e-15) and abs(rot["theta"] - theta) < 1e-14
+        assert np.allclose(rot["axis"], axis, atol=4e-16 * G) and abs(rot["theta"] - theta) < 1e-14
         assert np.allclose(rot["R_vote"], oracle.rodrigues(axis, theta), atol=1e-14)
         V, V_lo, V_hi = oracle.vote_set(av_, b, J, window)
         gv = g["vote_set"][a]
