@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sprot", choices=["sprot", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="correspondences of the oracle baseline sample (default 2000 per host core)")
     return ap.parse_args()
@@ -304,7 +306,8 @@ def run_sprot(args):
         "gpu_launches": int(launches), "step_ms_min": min(step_ms), "step_ms_median": float(np.median(step_ms)),
     }
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(prob, G, J, tau, args.cpu_sample)
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(prob, G, J, tau, args.cpu_sample)
         if not args.no_extras:
             try:
                 out["multi_rotation"] = run_multi(B, dev)

@@ -103,7 +103,8 @@ size_t problem_footprint(int64_t n, int G, int J, int k);
 
 // ---- launchers -------------------------------------------------------------------------
 // Axis vote (vote_walk.cu). tile_bytes: the largest band tile of the launch; the kernel adds
-// its per-warp circle tables (vote_table_bytes()) to the dynamic shared memory.
+// its per-warp circle tables and per-lane dummy vote words (vote_table_bytes()) to the dynamic
+// shared memory.
 int vote_table_bytes();
 // eps-band accumulator of Eq. 9 (vote_eps.cu): same items, tiles and partials as the curve vote.
 void launch_axis_vote_eps(const VoteItem* items, int n_items, const InstDev* insts, int* counter, int grid_ctas,

@@ -16,7 +16,8 @@
 // coordinates, three roundings). The two cells of extreme points are voted directly.
 //
 // Work split. A CTA owns one row band of the accumulator as 16-bit counters in shared
-// memory (columns 2j and 2j+1 share a 32-bit word), incremented with red.shared.add.u32. A
+// memory (columns 2j and 2j+1 share a 32-bit word), incremented with red.shared.add.u32
+// (unconditionally: a vote that fails its test is sent to a per-lane dummy word). A
 // warp loads 32 circles; in phase A each lane prepares its own circle for the band (piece
 // ranges culled to the band and the grid, extreme cells voted) and stores it in a per-warp
 // table. In phase B the pieces of all 32 circles are concatenated and each lane takes an
@@ -261,7 +262,7 @@ __device__ __forceinline__ bool circle_of(const float* __restrict__ P, const flo
 }
 
 // Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
-constexpr int kSeg = 16;
+constexpr int kSeg = 24;
 constexpr int kWalkers = 3;
 
 __device__ __forceinline__ int segments_of(uint32_t pk) {
@@ -315,12 +316,13 @@ struct Walker {
   float d3, dM2, dN2, xe, gx, yb, h, dys;
 };
 
-__device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(
-          (uint32_t)(hb << 1) & ~3u),
-      "r"(inc), "r"((int)cond)
-      : "memory");
+// A vote whose condition fails goes to the lane's own dummy word (32 words behind the warp
+// tables, never read), so every vote is one unconditional atomic: no predicate is formed
+// from the condition, and lanes never diverge around the atomics. The dummy words of the
+// 32 lanes lie in 32 distinct banks.
+__device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc, uint32_t dummy) {
+  const uint32_t addr = cond ? ((uint32_t)(hb << 1) & ~3u) : dummy;
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc) : "memory");
 }
 
 // Decodes segment sid of the batch and places the walker on its first cell (len = 0 if none).
@@ -422,16 +424,16 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
 // is still beyond the following edge (a second crossing in the same step, which is rare).
 // A walker that leaves the grid never returns (each piece is monotone along its minor axis)
 // and its votes are masked by the window test, so the common step does not stop at the edge.
-__device__ __forceinline__ bool step_walker(Walker& w, int i) {
+__device__ __forceinline__ bool step_walker(Walker& w, int i, uint32_t dummy) {
   const bool act = i < w.len;
-  vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
+  vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
   const bool mv = act && w.gx < -w.h;
   w.rel += mv ? w.dir : 0;
   w.hb += mv ? w.dmin : 0;
   w.inc ^= mv ? (w.fmaj ^ 0x10001u) : 0u;
   w.yb += mv ? w.dys : 0.f;
   w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-  vote_if(mv && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
+  vote_if(mv && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
   return mv && w.gx < -w.h;
 }
 
@@ -444,7 +446,8 @@ __device__ __forceinline__ void more_crossings(Walker& w) {
     w.inc ^= w.fmaj ^ 0x10001u;
     w.yb += w.dys;
     w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-    vote_if((unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc);
+    if ((unsigned)w.rel <= (unsigned)w.span)  // the rare loop keeps a plain branch
+      asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)(w.hb << 1) & ~3u), "r"(w.inc) : "memory");
   }
 }
 
@@ -460,7 +463,7 @@ __device__ __forceinline__ void advance(Walker& w, float step) {
 // so that every lane decodes its segments and solves their start quadratics at the same time
 // and walks independent segments in lock step.
 __device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
-                                           int lane) {
+                                           int lane, uint32_t dummy) {
   for (int base = 0; base < total_segs; base += 32 * kWalkers) {
     Walker w[kWalkers];
     int longest = 0;
@@ -474,7 +477,7 @@ __device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, i
       bool more[kWalkers], any = false;
 #pragma unroll
       for (int j = 0; j < kWalkers; ++j) {
-        more[j] = step_walker(w[j], i);
+        more[j] = step_walker(w[j], i, dummy);
         any |= more[j];
       }
       if (__any_sync(kFull, any)) {
@@ -496,6 +499,8 @@ __global__ void __launch_bounds__(kWalkThreads, 1)
   __shared__ int s_item, s_next;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* tab = smem + tile_words + warp * kTabWords;
+  // this lane's dummy word for votes that fail their test
+  const uint32_t dummy = (uint32_t)__cvta_generic_to_shared(smem + tile_words + kWalkWarps * kTabWords + lane);
   for (;;) {
     if (threadIdx.x == 0) {
       s_item = atomicAdd(counter, 1);
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(kWalkThreads, 1)
       }
       __syncwarp();
       // phase B: the whole batch
-      if (total > 0) walk_batch(B, tab, total, lane);
+      if (total > 0) walk_batch(B, tab, total, lane, dummy);
       __syncwarp();
       base = nbase;
     }
@@ -594,7 +599,7 @@ __global__ void __launch_bounds__(1024) k_probe_atomics(int iters, uint32_t* sin
 
 }  // namespace
 
-int vote_table_bytes() { return kWalkWarps * kTabWords * 4; }
+int vote_table_bytes() { return kWalkWarps * kTabWords * 4 + 32 * 4; }  // tables + dummy words
 
 void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
                            int grid_ctas, int tile_bytes, cudaStream_t st) {
