@@ -304,15 +304,18 @@ __device__ __forceinline__ void store_rec(uint32_t* tab, int lane, const Prepare
 
 
 // One walker: a segment of one piece, advanced one major step per iteration. The cell is
-// tracked as a half-word index hb into the tile (two u16 counters per word, offset so that
-// the word's shared address is (hb << 1) & ~3) with the increment inc = 1 or 0x10000 for
-// its half, and as its minor coordinate rel relative to the piece's window. The crossing
+// tracked as the shared-memory byte address hb of its 16-bit counter (two counters per word,
+// so the word's address is hb & ~3) with the increment inc = 1 or 0x10000 for its half, and
+// as its minor coordinate rel relative to the piece's window. The state changes of a step
+// are multiply-adds by the 0/1 move flag rather than selects (they leave the integer ALU
+// pipe, the kernel's busiest, for the FMA pipe). The crossing
 // test is gx < -h (F < 0) for every piece: the coefficients of odd pieces are negated, which
 // negates F exactly, and without flush to zero the sign of a rounded sum is the sign of the
 // exact one.
 struct Walker {
   int len, hb, rel, span, rlim, dmaj, dmin, dir;
   uint32_t inc, fmaj;  // fmaj: the flip of inc on a major step (the minor flip is its complement)
+  int tog;             // 1 if a minor step changes the column (swaps the half of inc)
   float d3, dM2, dN2, xe, gx, yb, h, dys;
 };
 
@@ -321,7 +324,7 @@ struct Walker {
 // from the condition, and lanes never diverge around the atomics. The dummy words of the
 // 32 lanes lie in 32 distinct banks.
 __device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc, uint32_t dummy) {
-  const uint32_t addr = cond ? ((uint32_t)(hb << 1) & ~3u) : dummy;
+  const uint32_t addr = dummy + (uint32_t)cond * (((uint32_t)hb & ~3u) - dummy);  // cond ? word : dummy
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc) : "memory");
 }
 
@@ -339,6 +342,7 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.dir = 1;
   w.inc = 1u;
   w.fmaj = 0u;
+  w.tog = 0;
   w.d3 = w.dM2 = w.dN2 = w.xe = w.gx = w.yb = w.h = w.dys = 0.f;
   if (sid >= total_segs) return;
   // the circle: the largest k with first_segment[k] <= sid
@@ -403,11 +407,12 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.rlim = (dir > 0 ? G : -1) - wlo;  // the rare-crossing loop stops at the grid edge
   const int W2 = 2 * B.W;              // half-words per tile row
   const int row = tr ? c : r, col = tr ? r : c;
-  w.hb = (row - B.R0) * W2 + col + (int)(B.sbase >> 1);
+  w.hb = 2 * ((row - B.R0) * W2 + col) + (int)B.sbase;
   w.inc = (col & 1) ? 0x10000u : 1u;
   w.fmaj = tr ? 0u : 0x10001u;
-  w.dmaj = tr ? W2 : 1;
-  w.dmin = tr ? dir : dir * W2;
+  w.tog = tr ? 1 : 0;
+  w.dmaj = tr ? 2 * W2 : 2;
+  w.dmin = tr ? 2 * dir : 2 * dir * W2;
   const float sg = flip ? -1.f : 1.f;
   w.d3 = sg * d3;
   w.dM2 = sg * dM2;
@@ -428,9 +433,11 @@ __device__ __forceinline__ bool step_walker(Walker& w, int i, uint32_t dummy) {
   const bool act = i < w.len;
   vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
   const bool mv = act && w.gx < -w.h;
-  w.rel += mv ? w.dir : 0;
-  w.hb += mv ? w.dmin : 0;
-  w.inc ^= mv ? (w.fmaj ^ 0x10001u) : 0u;
+  const int m = (int)mv;
+  w.rel += m * w.dir;
+  w.hb += m * w.dmin;
+  // a column change swaps the half: 1 <-> 0x10000, i.e. inc -> 0x10001 - inc
+  w.inc += (uint32_t)(m & w.tog) * (0x10001u - 2u * w.inc);
   w.yb += mv ? w.dys : 0.f;
   w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
   vote_if(mv && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
@@ -447,7 +454,7 @@ __device__ __forceinline__ void more_crossings(Walker& w) {
     w.yb += w.dys;
     w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
     if ((unsigned)w.rel <= (unsigned)w.span)  // the rare loop keeps a plain branch
-      asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)(w.hb << 1) & ~3u), "r"(w.inc) : "memory");
+      asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)w.hb & ~3u), "r"(w.inc) : "memory");
   }
 }
 
