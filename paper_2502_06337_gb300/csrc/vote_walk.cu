@@ -20,11 +20,12 @@
 // (unconditionally: a vote that fails its test is sent to a per-lane dummy word). A
 // warp loads 32 circles; in phase A each lane prepares its own circle for the band (piece
 // ranges culled to the band and the grid, extreme cells voted) and stores it in a per-warp
-// table. In phase B the pieces of all 32 circles are concatenated and each lane takes an
-// equal share of their major steps, so a lane restarts (one quadratic solve) only at piece
-// boundaries. One iteration of a lane votes one cell and then either crosses one lattice
-// edge of the minor axis -- when the piece is beyond that edge at the exit line, i.e. when
-// F at the lattice corner has the sign of "beyond" -- or advances one major step. F is
+// table. In phase B the pieces of all 32 circles are cut into segments of at most kSeg major
+// steps, dealt out in rounds of kWalkers segments per lane; a walker starts a segment with
+// one quadratic solve and walks it in lock step with the warp. One step of a walker votes
+// one cell and then either crosses one lattice edge of the minor axis -- when the piece is
+// beyond that edge at the exit line, i.e. when F at the lattice corner has the sign of
+// "beyond" -- or advances one major step. F is
 // evaluated as g(x) + h(y) with g, h updated only when x or y changes, three roundings in
 // all. Decisions whose F is within a few float32 roundings of zero lie inside the band
 // where the closed-cell test may go either way; all others match the exact test.
@@ -263,7 +264,7 @@ __device__ __forceinline__ bool circle_of(const float* __restrict__ P, const flo
 
 // Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
 constexpr int kSeg = 24;
-constexpr int kWalkers = 3;
+constexpr int kWalkers = 2;  // independent walkers per lane (instruction-level parallelism)
 
 __device__ __forceinline__ int segments_of(uint32_t pk) {
   const int l = (int)(pk >> 16) - (int)(pk & 0xffffu);
@@ -330,7 +331,7 @@ __device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc, uint32_
 
 // Decodes segment sid of the batch and places the walker on its first cell (len = 0 if none).
 __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab, int total_segs,
-                                             int sid, Walker& w) {
+                                             int sid, int part, int nparts, Walker& w) {
   const int G = B.G;
   const float step = B.step;
   w.len = 0;
@@ -368,8 +369,13 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   const uint32_t pk = tab[(5 + p) * 32 + k];
   const int lo = (int)(pk & 0xffffu);
   const int plen = (int)(pk >> 16) - lo;
-  const int c = lo + seg * kSeg;
+  int c = lo + seg * kSeg;
   int len = min(kSeg, plen - seg * kSeg);
+  if (nparts > 1) {  // part `part` of nparts consecutive parts of the segment
+    const int sub = nparts == 2 ? (len + 1) >> 1 : (len + 2) / 3;
+    c += part * sub;
+    len = max(0, min(sub, len - part * sub));
+  }
   const float d1 = __uint_as_float(tab[0 * 32 + k]), d2 = __uint_as_float(tab[1 * 32 + k]);
   const float inv3 = __uint_as_float(tab[3 * 32 + k]);
   const float d3 = __uint_as_float(tab[2 * 32 + k]);
@@ -472,11 +478,18 @@ __device__ __forceinline__ void advance(Walker& w, float step) {
 __device__ __forceinline__ void walk_batch(const Band& B, const uint32_t* tab, int total_segs,
                                            int lane, uint32_t dummy) {
   for (int base = 0; base < total_segs; base += 32 * kWalkers) {
+    // The last deal of a batch: when at most half the walkers would get a segment, each
+    // remaining segment is cut into two or three consecutive parts, so that more walkers
+    // share it and the deal takes fewer rounds.
+    const int rem = total_segs - base;
+    const int nparts = rem > 16 * kWalkers ? 1 : (rem > 32 * kWalkers / 3 ? 2 : 3);
     Walker w[kWalkers];
     int longest = 0;
 #pragma unroll
     for (int j = 0; j < kWalkers; ++j) {
-      start_walker(B, tab, total_segs, base + 32 * j + lane, w[j]);
+      const int t = 32 * j + lane;
+      const int q = nparts == 1 ? t : (nparts == 2 ? t >> 1 : t / 3);
+      start_walker(B, tab, total_segs, base + q, t - q * nparts, nparts, w[j]);
       longest = max(longest, w[j].len);
     }
     const int rounds = __reduce_max_sync(kFull, (unsigned)longest);
