@@ -95,6 +95,22 @@ int sm_count(int dev) {
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// The device address of a host buffer of `bytes` bytes when all of it lies in one pinned,
+// device-mapped allocation (cudaHostAlloc / cudaMallocHost / cudaHostRegister); else null.
+const float* mapped_host(const void* p, size_t bytes) {
+  cudaPointerAttributes a{}, b{};
+  const char* last = static_cast<const char*>(p) + bytes - 1;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+    return nullptr;
+  if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+    return nullptr;  // not one contiguous mapping
+  return static_cast<const float*>(a.devicePointer);
+}
+
 int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, int k) {
   if (!P || !Q || !p) return SPROT_E_INVAL;
   if (n < 1 || n > (int64_t)1 << 31) return SPROT_E_INVAL;
@@ -182,6 +198,16 @@ struct Workspace {
   // events recorded around the vote kernel inside every captured sequence (solves on a
   // workspace are serialised and synchronised, so one pair serves all its graphs)
   cudaEvent_t tv0 = nullptr, tv1 = nullptr;
+  // second stream for host-input copies that overlap the axis vote, with its fork/join events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool aux_stream() {
+    if (!aux && cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess) aux = nullptr;
+    if (!fork && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) fork = nullptr;
+    if (!join && cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) join = nullptr;
+    if (!(aux && fork && join)) cudaGetLastError();
+    return aux && fork && join;
+  }
   bool timing_events() {
     if (!tv0 && cudaEventCreate(&tv0) != cudaSuccess) tv0 = nullptr;
     if (!tv1 && cudaEventCreate(&tv1) != cudaSuccess) tv1 = nullptr;
@@ -196,6 +222,9 @@ struct Workspace {
     drop_graphs();
     if (tv0) cudaEventDestroy(tv0);
     if (tv1) cudaEventDestroy(tv1);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (aux) cudaStreamDestroy(aux);
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
@@ -462,6 +491,26 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   char* D = ws->dev;
   char* H = ws->host;
 
+  // Host inputs in pinned, device-mapped memory: the axis vote reads them directly over the
+  // host link while a second stream copies them to the device for the later passes, so the
+  // copy overlaps the vote. Other host inputs are copied first.
+  std::vector<std::pair<const float*, const float*>> vote_src(m, {nullptr, nullptr});
+  bool overlap = false;
+  for (int i = 0; i < m; ++i) {
+    const Problem& pb = probs[i];
+    if (!pb.host_io) continue;
+    const float* pv = mapped_host(pb.P, (size_t)pb.n * 12);
+    const float* qv = mapped_host(pb.Q, (size_t)pb.n * 12);
+    if (pv && qv) {
+      vote_src[i] = {pv, qv};
+      overlap = true;
+    }
+  }
+  if (overlap && !ws->aux_stream()) {
+    overlap = false;
+    vote_src.assign(m, {nullptr, nullptr});
+  }
+
   // ---- tables -------------------------------------------------------------------------
   InstDev* hid = reinterpret_cast<InstDev*>(H + o_inst);
   for (int i = 0; i < m; ++i) {
@@ -471,6 +520,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     std::memset(&d, 0, sizeof(d));
     d.P = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_P) : pb.P;
     d.Q = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_Q) : pb.Q;
+    d.Pv = vote_src[i].first ? vote_src[i].first : d.P;
+    d.Qv = vote_src[i].second ? vote_src[i].second : d.Q;
     d.n = ip.n;
     d.G = ip.G;
     d.J = ip.J;
@@ -515,13 +566,17 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   const StreamItem* dsit = reinterpret_cast<const StreamItem*>(D + o_sit);
   int* dcounter = reinterpret_cast<int*>(D + o_counter);
   char* Hres = H + align_up(header_end);
-  // caller pointers outside the workspace (debug exports, host inputs) would be baked into a
-  // graph: those calls run directly
+  // Caller pointers outside the workspace are baked into a graph. Debug exports and pageable
+  // host inputs run directly; pinned host inputs (and outputs) are part of the graph's key.
   bool direct_only = !graphs || !ws->timing_events();
-  for (int i = 0; i < m; ++i) direct_only |= probs[i].dbg != nullptr || probs[i].host_io;
+  for (int i = 0; i < m; ++i) direct_only |= probs[i].dbg != nullptr || (probs[i].host_io && !vote_src[i].first);
   std::optional<VoteTimer> vt;
   auto enqueue = [&](bool direct) -> bool {
     bool ok = true;
+    if (overlap) {  // the second stream starts after everything already ordered on st
+      ok &= ck(cudaEventRecord(ws->fork, st));
+      ok &= ck(cudaStreamWaitEvent(ws->aux, ws->fork, 0));
+    }
     ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
     ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
     for (int i = 0; i < m; ++i) {
@@ -529,10 +584,12 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
       if (pb.dbg && pb.dbg->hist)
         ok &= ck(cudaMemsetAsync(pb.dbg->hist, 0, sizeof(uint32_t) * plan[i].k * plan[i].J, st));
       if (pb.host_io) {
-        ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
-        ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, st));
+        cudaStream_t cs = vote_src[i].first ? ws->aux : st;
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, cs));
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, cs));
       }
     }
+    if (overlap) ok &= ck(cudaEventRecord(ws->join, ws->aux));
     if (!ok) return false;
     if (direct)
       vt.emplace(st);
@@ -544,6 +601,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
       vt->stop(st);
     else
       ok &= ck(cudaEventRecord(ws->tv1, st));
+    if (overlap) ok &= ck(cudaStreamWaitEvent(st, ws->join, 0));  // the later passes read P, Q
     // each kernel's last block per instance finishes that instance's stage (peaks; angle peak
     // and Rodrigues; the two Kabsch solves)
     launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
@@ -572,7 +630,18 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
         (uint64_t)(uintptr_t)D, (uint64_t)(uintptr_t)H, header_end, o_zero, zero_end, o_res, res_end,
         vitems.size(), ritems.size(), sitems.size(), (uint64_t)m, (uint64_t)max_k, (uint64_t)max_J,
         (uint64_t)vote_tile, (uint64_t)nsm};
-    ok = run_graph(ws, key, st, [&] { return enqueue(false); });
+    std::vector<uint64_t> k2 = key;
+    for (int i = 0; i < m; ++i) {
+      if (!probs[i].host_io) continue;
+      // the host buffers the graph copies from and to, the copy sizes and staging offsets
+      for (const void* q : {(const void*)probs[i].P, (const void*)probs[i].Q, (const void*)probs[i].mask,
+                            (const void*)probs[i].labels})
+        k2.push_back((uint64_t)(uintptr_t)q);
+      for (uint64_t v : {(uint64_t)probs[i].n, (uint64_t)plan[i].o_P, (uint64_t)plan[i].o_Q,
+                         (uint64_t)plan[i].o_mask, (uint64_t)plan[i].o_labels})
+        k2.push_back(v);
+    }
+    ok = run_graph(ws, k2, st, [&] { return enqueue(false); });
   }
   if (!ok || !ck(cudaStreamSynchronize(st))) return SPROT_E_CUDA;
   if (vt) {
@@ -654,6 +723,8 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   std::memset(&d, 0, sizeof(d));
   d.P = P;
   d.Q = Q;
+  d.Pv = P;
+  d.Qv = Q;
   d.n = n;
   d.G = G;
   d.k = 1;

@@ -36,6 +36,10 @@ struct DevRot {
 struct InstDev {
   const float* P;
   const float* Q;
+  // the axis vote's source of P and Q: P and Q, or the caller's pinned host buffers, which the
+  // vote reads over the host link while P and Q are being copied to the device
+  const float* Pv;
+  const float* Qv;
   int64_t n;
   int32_t G, J, k, w, window;
   int32_t n_bands, S;            // row bands and circle slices of the axis vote

@@ -545,8 +545,8 @@ __global__ void __launch_bounds__(kWalkThreads, 1)
     for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
     __syncthreads();
 
-    const float* __restrict__ P = D.P;
-    const float* __restrict__ Q = D.Q;
+    const float* __restrict__ P = D.Pv;  // device memory, or pinned host memory (see InstDev)
+    const float* __restrict__ Q = D.Qv;
     const int64_t count = I.c1 - I.c0;
     // the warp's batches of 32 circles; the next batch's pairs are loaded while this one is
     // walked

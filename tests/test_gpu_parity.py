@@ -162,6 +162,73 @@ def test_host_pointers_match_device(lib):
     assert np.array_equal(mask_d.cpu().numpy(), mask_h)
 
 
+@pytest.mark.parametrize("n,offset", [(5000, 0), (5000, 777), (1_000_000, 0)])
+def test_pinned_host_pointers_match_device(lib, n, offset):
+    """Host inputs in pinned memory are read by the axis vote directly while a second stream
+    copies them to the device; the results must equal the device-pointer solve. ``offset``
+    places the buffers inside a larger pinned allocation."""
+    from paper_2502_06337_gb300 import binding as B
+    import torch
+
+    prob = synth.make_problem(n, (0.1,), 0.01, seed=5)
+    prm = B.make_params(grid=512 if n > 10**5 else 256, angle_bins=720, tau=0.052)
+    mask_d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    a = B.estimate_rotation(torch.from_numpy(prob.P).cuda(), torch.from_numpy(prob.Q).cuda(), prm, mask=mask_d)
+    Pbig = torch.zeros(n + offset, 3, dtype=torch.float32).pin_memory()
+    Qbig = torch.zeros(n + offset, 3, dtype=torch.float32).pin_memory()
+    Pbig[offset:] = torch.from_numpy(prob.P)
+    Qbig[offset:] = torch.from_numpy(prob.Q)
+    mask_h = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    prm.flags = B.HOST_PTRS
+    for _ in range(3):  # direct, then captured as a graph, then replayed
+        b = B.estimate_rotation(Pbig[offset:].numpy(), Qbig[offset:].numpy(), prm, mask=mask_h.numpy())
+        assert a["cell"] == b["cell"] and a["bin"] == b["bin"] and a["n_inliers"] == b["n_inliers"]
+        assert a["axis_votes"] == b["axis_votes"] and a["angle_votes"] == b["angle_votes"]
+        assert np.array_equal(a["R"], b["R"])
+        assert np.array_equal(mask_d.cpu().numpy(), mask_h.numpy())
+
+
+def test_pinned_host_buffers_reused_with_new_contents_and_sizes(lib):
+    """The same pinned buffers solved with new contents and a smaller n in between (a replayed
+    graph must copy the current contents, and a new size must not replay the old sequence)."""
+    from paper_2502_06337_gb300 import binding as B
+    import torch
+
+    nmax = 40000
+    Ph = torch.zeros(nmax, 3, dtype=torch.float32).pin_memory()
+    Qh = torch.zeros(nmax, 3, dtype=torch.float32).pin_memory()
+    prm = B.make_params(grid=256, angle_bins=360, tau=0.05)
+    prm_h = B.make_params(grid=256, angle_bins=360, tau=0.05, flags=B.HOST_PTRS)
+    for rep in range(3):
+        for seed, n in ((61, nmax), (62, nmax), (63, 25000)):
+            prob = synth.make_problem(n, (0.2,), 0.01, seed=seed)
+            Ph[:n] = torch.from_numpy(prob.P)
+            Qh[:n] = torch.from_numpy(prob.Q)
+            want = B.estimate_rotation(torch.from_numpy(prob.P).cuda(), torch.from_numpy(prob.Q).cuda(), prm)
+            got = B.estimate_rotation(Ph[:n].numpy(), Qh[:n].numpy(), prm_h)
+            assert got["cell"] == want["cell"] and got["bin"] == want["bin"]
+            assert got["n_inliers"] == want["n_inliers"] and np.array_equal(got["R"], want["R"])
+
+
+def test_pinned_host_pointers_multi_rotation(lib):
+    from paper_2502_06337_gb300 import binding as B
+    import torch
+
+    prob = synth.make_problem(30000, (0.2, 0.2, 0.2), 0.01, seed=6)
+    prm = B.make_params(grid=256, angle_bins=360, k=3, nms_deg=2.0, tau=0.05)
+    lab_d = torch.zeros(prob.n, dtype=torch.int32, device="cuda")
+    a = B.estimate_rotations(torch.from_numpy(prob.P).cuda(), torch.from_numpy(prob.Q).cuda(), prm, labels=lab_d)
+    Ph = torch.from_numpy(prob.P).pin_memory()
+    Qh = torch.from_numpy(prob.Q).pin_memory()
+    lab_h = torch.zeros(prob.n, dtype=torch.int32).pin_memory()
+    prm.flags = B.HOST_PTRS
+    b = B.estimate_rotations(Ph.numpy(), Qh.numpy(), prm, labels=lab_h.numpy())
+    assert len(a) == len(b) == 3
+    for x, y in zip(a, b):
+        assert x["cell"] == y["cell"] and x["bin"] == y["bin"] and np.array_equal(x["R"], y["R"])
+    assert np.array_equal(lab_d.cpu().numpy(), lab_h.numpy())
+
+
 def test_determinism_permutation_and_swap(lib):
     prob = synth.make_problem(20000, (0.2,), 0.01, seed=8)
     G = 256
