@@ -242,26 +242,6 @@ __device__ __forceinline__ bool circle_from(const float* r, float& d1, float& d2
   return true;
 }
 
-// p - q scaled by a power of two so that max |d_k| is in [1, 2), signed so d3 >= 0.
-__device__ __forceinline__ bool circle_of(const float* __restrict__ P, const float* __restrict__ Q,
-                                          int64_t i, float& d1, float& d2, float& d3) {
-  d1 = __ldg(P + 3 * i) - __ldg(Q + 3 * i);
-  d2 = __ldg(P + 3 * i + 1) - __ldg(Q + 3 * i + 1);
-  d3 = __ldg(P + 3 * i + 2) - __ldg(Q + 3 * i + 2);
-  const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
-  if (m == 0.f) return false;
-  const int e = ilogbf(m);
-  d1 = scalbnf(d1, -e);
-  d2 = scalbnf(d2, -e);
-  d3 = scalbnf(d3, -e);
-  if (d3 < 0.f) {
-    d1 = -d1;
-    d2 = -d2;
-    d3 = -d3;
-  }
-  return true;
-}
-
 // Segment length of phase B: every piece is cut into segments of at most kSeg major steps.
 constexpr int kSeg = 24;
 constexpr int kWalkers = 2;  // independent walkers per lane (instruction-level parallelism)

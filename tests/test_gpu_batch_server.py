@@ -35,6 +35,7 @@ def _instances():
         dict(n=20000, fr=(0.2, 0.2, 0.2), sigma=0.01, seed=14, grid=256, k=3),
         dict(n=1, fr=(1.0,), sigma=0.0, seed=15, grid=64, k=1),
         dict(n=300, fr=(0.7,), sigma=0.02, seed=16, grid=16, k=2),
+        dict(n=3000, fr=(0.4,), sigma=0.01, seed=18, grid=1024, k=1),
     ]
     out = []
     for s in specs:

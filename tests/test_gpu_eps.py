@@ -32,7 +32,7 @@ def _check(g, ev):
 
 
 @pytest.mark.parametrize("G,eps,n", [(16, 0.05, 300), (64, 0.01, 700), (256, 0.003, 500), (512, 0.3, 120),
-                                     (512, 1e-9, 400), (64, 0.0, 333)])
+                                     (512, 1e-9, 400), (64, 0.0, 333), (1024, 0.002, 150), (2048, 0.001, 40)])
 def test_eps_vote_matches_oracle(lib, G, eps, n):
     prob = synth.make_problem(n, (0.4,), 0.01, seed=G + n)
     P, Q = prob.P.copy(), prob.Q.copy()

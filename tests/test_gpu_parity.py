@@ -312,6 +312,25 @@ def test_axis_vote_large_grids(lib, G, n):
     parity.check_grid(_gpu_grid(prob.P, prob.Q, G), av, f"G={G}")
 
 
+@pytest.mark.parametrize("G,n", [(1024, 1_000_000), (2048, 200_000)])
+def test_large_grids_at_scale(lib, G, n):
+    """The headline pair distribution at G = 1024 (11 row bands) and G = 2048 (45 bands): the
+    peak's 5 x 5 neighbourhood, 16 random rows x 8 random columns and 64 random cells against
+    the oracle's per-cell count over all pairs."""
+    prob = synth.make_problem(n, (0.1,), 0.01, seed=G)
+    g = _gpu_grid(prob.P, prob.Q, G)
+    row, col = divmod(int(np.argmax(g)), G)
+    rng = np.random.default_rng(G)
+    cells = [(row + dr, col + dc) for dr in range(-2, 3) for dc in range(-2, 3)]
+    cells += [(int(r), int(c)) for r in rng.integers(0, G, 16) for c in rng.integers(0, G, 8)]
+    cells += [(int(r), int(c)) for r, c in zip(rng.integers(0, G, 64), rng.integers(0, G, 64))]
+    rr, cc = zip(*[(r, c) for r, c in cells if 0 <= r < G and 0 <= c < G])
+    cnt, lo, hi = oracle.cell_votes(prob.P, prob.Q, G, rr, cc)
+    got = g[list(rr), list(cc)]
+    assert np.all(got >= lo) and np.all(got <= hi)
+    assert np.array_equal(got[lo == hi], cnt[lo == hi])
+
+
 @pytest.mark.parametrize("G", [16, 32, 512])
 def test_axis_vote_small_radius_circles(lib, G):
     """Circles of radius close to 1 (|d3| dominant): at coarse grids the rows next to their

@@ -46,6 +46,15 @@ def test_subcell_multi_rotation_parity(lib):
     parity.check_solve(prob.P, prob.Q, g, 256, 360, k=3, nms=2.0, subcell=True)
 
 
+def test_subcell_many_peaks_on_a_small_grid(lib):
+    """k = 8 (the maximum) on a 16 x 16 grid with two rotations and a 10-degree radius:
+    suppressed neighbours can exceed a later peak, so clamped offsets occur."""
+    prob = synth.make_problem(3000, (0.3, 0.3), 0.01, seed=45)
+    g = parity.run_gpu(prob.P, prob.Q, 16, 90, k=8, nms=10.0, subcell=True)
+    assert 2 <= len(g["rots"]) <= 8
+    parity.check_solve(prob.P, prob.Q, g, 16, 90, k=8, nms=10.0, subcell=True)
+
+
 def test_subcell_peak_on_the_grid_border(lib):
     """A noise-free problem whose axis projects into row 0 (v within the first cell): the peak
     lies on the lower border, so the v offset is 0 and the u offset is the oracle's. Every
