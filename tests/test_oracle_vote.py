@@ -600,3 +600,79 @@ def test_subcell_axis_is_closer_to_the_true_axis():
         better += e1 < e0
     assert np.mean(sub) < 0.6 * np.mean(centre)
     assert better >= 12
+
+
+# ---- per-cell evaluators, vote set, labels, skew ----------------------------------------
+
+def _mixed_pairs(n, seed):
+    prob = synth.make_problem(n, (0.4,), 0.01, seed=seed)
+    P, Q = prob.P.copy(), prob.Q.copy()
+    Q[0] = P[0]                                              # degenerate
+    Q[1] = P[1] + np.array([0.0, 0.0, 0.5], np.float32)      # the unit circle
+    Q[2] = P[2] + np.array([0.3, -0.4, 0.0], np.float32)     # a line through the origin
+    return P, Q
+
+
+def test_cell_votes_equal_the_whole_grid():
+    """cell_votes loops over cells (all circles at once); axis_vote loops over circles (all
+    cells at once): on every cell of a 32 x 32 grid they must agree, bounds included."""
+    P, Q = _mixed_pairs(300, 90)
+    G = 32
+    av = ov.axis_vote(P, Q, G)
+    rows, cols = np.divmod(np.arange(G * G), G)
+    cnt, lo, hi = ov.cell_votes(P, Q, G, rows, cols)
+    assert np.array_equal(cnt, av["grid"].ravel())
+    assert np.array_equal(lo, av["lo"].ravel()) and np.array_equal(hi, av["hi"].ravel())
+
+
+def test_eps_cell_votes_equal_the_whole_grid():
+    P, Q = _mixed_pairs(120, 91)
+    G, eps = 32, 0.03
+    ev = ov.eps_axis_vote(P, Q, G, eps)
+    rows, cols = np.divmod(np.arange(G * G), G)
+    cnt, lo, hi = ov.eps_cell_votes(P, Q, G, eps, rows, cols)
+    assert np.array_equal(cnt, ev["grid"].ravel())
+    assert np.array_equal(lo, ev["lo"].ravel()) and np.array_equal(hi, ev["hi"].ravel())
+
+
+def test_vote_set_wraps_around_and_bounds_flagged_pairs():
+    """Peak bin 0 of J = 10 with a window of 1: bins 9, 0 and 1 are in the set (circular).
+    A flagged voter two bins out may belong (upper bound only); a flagged voter one bin out
+    may fall out (lower bound excludes it); a non-member never belongs."""
+    J = 10
+    binv = np.array([0, 1, 9, 2, 8, 5, -1, 2, 1, 0])
+    member = np.array([1, 1, 1, 1, 1, 1, 0, 1, 1, 0], bool)
+    flag = np.array([0, 0, 0, 0, 0, 0, 0, 1, 1, 0], bool)
+    av = dict(bin=binv, member=member, member_lo=member & ~flag, member_hi=member | flag, bin_flag=flag)
+    V, V_lo, V_hi = ov.vote_set(av, 0, J, 1)
+    assert V.tolist() == [1, 1, 1, 0, 0, 0, 0, 0, 1, 0]
+    assert V_lo.tolist() == [1, 1, 1, 0, 0, 0, 0, 0, 0, 0]   # the flagged one-bin voter may fall out
+    assert V_hi.tolist() == [1, 1, 1, 0, 0, 0, 0, 1, 1, 0]   # the flagged two-bin voter may come in
+    assert np.all(V_lo <= V) and np.all(V <= V_hi)
+
+
+def test_assign_labels_on_constructed_pairs():
+    """R_0 = I, R_1 = 90 degrees about z. Pairs fitting R_0, fitting R_1, fitting neither, and
+    points on the z axis (fixed by both: residual 0 under each, so the tie goes to 0 and is
+    flagged), and a pair whose residual is tau itself (flagged)."""
+    rng = np.random.default_rng(92)
+    R1 = Rotation.from_rotvec([0.0, 0.0, math.pi / 2]).as_matrix()
+    P = rng.uniform(-1.0, 1.0, (40, 3))
+    P[30:35, :2] = 0.0  # on the z axis
+    Q = P.copy()
+    Q[10:20] = P[10:20] @ R1.T
+    Q[20:30] = P[20:30] + rng.choice([-1.0, 1.0], (10, 3)) * 0.5  # far from both
+    tau = 0.05
+    Q[35] = P[35] + np.array([tau, 0.0, 0.0])  # residual exactly tau under R_0
+    labels, flag = ov.assign_labels(P, Q, [np.eye(3), R1], tau)
+    assert np.all(labels[:10] == 0) and np.all(labels[10:20] == 1) and np.all(labels[20:30] == -1)
+    assert np.all(labels[30:35] == 0) and np.all(flag[30:35])
+    assert flag[35] and labels[35] in (0, -1)
+    assert not flag[:30].any()
+
+
+def test_skew_is_the_cross_product():
+    rng = np.random.default_rng(93)
+    for _ in range(20):
+        r, v = rng.standard_normal(3), rng.standard_normal(3)
+        assert np.allclose(oracle.geometry.skew(r) @ v, np.cross(r, v), atol=1e-15)
