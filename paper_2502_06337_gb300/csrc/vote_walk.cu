@@ -297,6 +297,7 @@ struct Walker {
   int len, hb, rel, span, rlim, dmaj, dmin, dir;
   uint32_t inc, fmaj;  // fmaj: the flip of inc on a major step (the minor flip is its complement)
   int tog;             // 1 if a minor step changes the column (swaps the half of inc)
+  bool in;             // the current cell lies in the piece's window (a major step keeps it)
   float d3, dM2, dN2, xe, gx, yb, h, dys;
 };
 
@@ -324,6 +325,7 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.inc = 1u;
   w.fmaj = 0u;
   w.tog = 0;
+  w.in = false;
   w.d3 = w.dM2 = w.dN2 = w.xe = w.gx = w.yb = w.h = w.dys = 0.f;
   if (sid >= total_segs) return;
   // the circle: the largest k with first_segment[k] <= sid
@@ -390,6 +392,7 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.len = len;
   w.dir = dir;
   w.rel = r - wlo;
+  w.in = (unsigned)w.rel <= (unsigned)w.span;
   w.rlim = (dir > 0 ? G : -1) - wlo;  // the rare-crossing loop stops at the grid edge
   const int W2 = 2 * B.W;              // half-words per tile row
   const int row = tr ? c : r, col = tr ? r : c;
@@ -417,16 +420,17 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
 // and its votes are masked by the window test, so the common step does not stop at the edge.
 __device__ __forceinline__ bool step_walker(Walker& w, int i, uint32_t dummy) {
   const bool act = i < w.len;
-  vote_if(act && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
+  vote_if(act && w.in, w.hb, w.inc, dummy);
   const bool mv = act && w.gx < -w.h;
   const int m = (int)mv;
   w.rel += m * w.dir;
   w.hb += m * w.dmin;
   // a column change swaps the half: 1 <-> 0x10000, i.e. inc -> 0x10001 - inc
-  w.inc += (uint32_t)(m & w.tog) * (0x10001u - 2u * w.inc);
+  w.inc += (uint32_t)(m * w.tog) * (0x10001u - 2u * w.inc);
   w.yb += mv ? w.dys : 0.f;
   w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-  vote_if(mv && (unsigned)w.rel <= (unsigned)w.span, w.hb, w.inc, dummy);
+  w.in = (unsigned)w.rel <= (unsigned)w.span;
+  vote_if(mv && w.in, w.hb, w.inc, dummy);
   return mv && w.gx < -w.h;
 }
 
@@ -439,7 +443,8 @@ __device__ __forceinline__ void more_crossings(Walker& w) {
     w.inc ^= w.fmaj ^ 0x10001u;
     w.yb += w.dys;
     w.h = fmaf(w.yb, fmaf(w.d3, w.yb, w.dN2), -w.d3);
-    if ((unsigned)w.rel <= (unsigned)w.span)  // the rare loop keeps a plain branch
+    w.in = (unsigned)w.rel <= (unsigned)w.span;
+    if (w.in)  // the rare loop keeps a plain branch
       asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)w.hb & ~3u), "r"(w.inc) : "memory");
   }
 }
