@@ -310,7 +310,8 @@ __device__ __forceinline__ void vote_if(bool cond, int hb, uint32_t inc, uint32_
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc) : "memory");
 }
 
-// Decodes segment sid of the batch and places the walker on its first cell (len = 0 if none).
+// Decodes segment sid of the batch and places the walker on its first cell (len = 0 if none);
+// with nparts > 1 the walker takes part `part` of nparts consecutive parts of the segment.
 __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab, int total_segs,
                                              int sid, int part, int nparts, Walker& w) {
   const int G = B.G;
