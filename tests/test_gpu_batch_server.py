@@ -172,3 +172,40 @@ def test_graph_replay_matches_direct_solves(lib):
         again, _ = B.estimate_batch(batch[::-1])
         _same(again[0], first[1], tol=0.0)
         _same(again[1], first[0], tol=0.0)
+
+
+def test_concurrent_calls_on_separate_streams(lib):
+    """Four host threads, each on its own CUDA stream, solve different problems repeatedly
+    (the workspaces, graph caches and launch counters are shared library state): every result
+    equals the same problem solved alone on the default stream."""
+    import threading
+
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    probs = [synth.make_problem(n, (0.2,), 0.01, seed=70 + t) for t, n in enumerate((20000, 50000, 3000, 120000))]
+    prm = B.make_params(grid=256, angle_bins=360, tau=0.05)
+    dev = [(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda()) for p in probs]
+    want = [B.estimate_rotation(P, Q, prm) for P, Q in dev]
+    errors, got = [], [[] for _ in dev]
+
+    def worker(t):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for _ in range(6):  # direct, captured, then replayed graphs on this stream
+                    got[t].append(B.estimate_rotation(dev[t][0], dev[t][1], prm))  # on s, the thread's current stream
+        except Exception as e:  # reported after the join
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(len(dev))]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t in range(len(dev)):
+        assert len(got[t]) == 6
+        for r in got[t]:
+            _same([r], [want[t]], tol=0.0)
