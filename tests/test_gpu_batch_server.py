@@ -209,3 +209,27 @@ def test_concurrent_calls_on_separate_streams(lib):
         assert len(got[t]) == 6
         for r in got[t]:
             _same([r], [want[t]], tol=0.0)
+
+
+def test_server_budget_admits_one_request_at_a_time(lib):
+    """Six requests of n = 20,000 at G = 128 (about 0.7 MB each with their workspace) under a
+    1 MB budget: each fits alone but no two fit together, so the server must queue them, admit
+    one at a time as memory frees up, and still give every request its result alone."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    probs = [synth.make_problem(20000, (0.3,), 0.01, seed=80 + i) for i in range(6)]
+    prm = B.make_params(grid=128, angle_bins=360, tau=0.05)
+    alone = [B.estimate_rotation(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda(), prm) for p in probs]
+    with B.Server(1 << 20, max_batch=8) as srv:
+        tickets = [srv.submit(p.P, p.Q, prm) for p in probs]
+        got = [srv.wait(t) for t in tickets]
+    spans = []
+    for g, a in zip(got, alone):
+        assert g["status"] == 0
+        _same(g["rotations"], [a])
+        spans.append((g["t_admit_ms"], g["t_done_ms"]))
+    spans.sort()
+    for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+        assert a1 >= d0 - 0.05, (a0, d0, a1, d1)  # admitted only after the previous one finished
