@@ -233,3 +233,30 @@ def test_server_budget_admits_one_request_at_a_time(lib):
     spans.sort()
     for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
         assert a1 >= d0 - 0.05, (a0, d0, a1, d1)  # admitted only after the previous one finished
+
+
+def test_batch_with_a_headline_instance_and_labels(lib):
+    """A batch holding the n = 10^6 headline problem beside a 3-rotation instance and two small
+    ones, with per-instance label outputs: every instance's rotations and labels equal those of
+    its solve alone."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    cfg = synth.HEADLINE
+    specs = [(synth.make_problem(cfg["n"], cfg["inlier_fracs"], cfg["sigma"], seed=0),
+              B.make_params(grid=512, angle_bins=720, tau=synth.default_tau(cfg["sigma"]))),
+             (synth.make_problem(30000, (0.2, 0.2, 0.2), 0.01, seed=90),
+              B.make_params(grid=256, angle_bins=360, k=3, nms_deg=2.0, tau=0.05)),
+             (synth.make_problem(4000, (0.5,), 0.01, seed=91), B.make_params(grid=0, tau=0.05)),
+             (synth.make_problem(150, (0.6,), 0.01, seed=92), B.make_params(grid=64, tau=0.05))]
+    dev = [(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda()) for p, _ in specs]
+    labs = [torch.full((p.n,), -7, dtype=torch.int32, device="cuda") for p, _ in specs]
+    res, grids = B.estimate_batch([(P, Q, prm, L) for (P, Q), (_, prm), L in zip(dev, specs, labs)])
+    for i, ((P, Q), (p, prm)) in enumerate(zip(dev, specs)):
+        alone_prm = B.make_params(grid=int(grids[i]), angle_bins=prm.angle_bins, k=prm.k, nms_deg=prm.nms_deg,
+                                  tau=prm.tau)
+        lab_alone = torch.full((p.n,), -7, dtype=torch.int32, device="cuda")
+        alone = B.estimate_rotations(P, Q, alone_prm, labels=lab_alone)
+        _same(res[i], alone)
+        assert torch.equal(labs[i], lab_alone)
