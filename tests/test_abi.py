@@ -73,3 +73,85 @@ def test_invalid_arguments_rejected_without_gpu(libpath):
     out = binding.Rotation()
     assert lib.sprot_estimate_rotation(None, None, 10, ctypes.byref(p), ctypes.byref(out), None, None) == binding.E_INVAL
     assert lib.sprot_axis_vote(None, None, 0, 256, None, None) == binding.E_INVAL
+
+
+# A stand-in input pointer that is never dereferenced: every call below must fail its host-side
+# argument checks (E_INVAL) before any CUDA call; a case that passed them would reach CUDA with it.
+FAKE = ctypes.c_void_p(0x1000)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("grid", 24), ("grid", 8), ("grid", 4096), ("grid", -256),
+    ("angle_bins", 1), ("angle_bins", 5000),
+    ("k", 0), ("k", 9),
+    ("tau", 0.0), ("tau", -1.0), ("tau", float("nan")), ("tau", float("inf")),
+    ("nms_deg", -1.0), ("nms_deg", float("nan")),
+    ("gate_window", -2), ("angle_window", -1),
+    ("flags", 0x80),
+])
+def test_every_parameter_is_checked_before_any_cuda_call(libpath, field, value):
+    lib = binding.load(libpath)
+    p = binding.make_params(grid=256, angle_bins=360, k=1, nms_deg=2.0, tau=0.05)
+    setattr(p, field, value)
+    outs = (binding.Rotation * 9)()
+    nf = ctypes.c_int32(0)
+    assert lib.sprot_estimate_rotations_ex(FAKE, FAKE, 1000, ctypes.byref(p), outs, ctypes.byref(nf), None, None,
+                                           None) == binding.E_INVAL
+    if field != "k":  # the single-rotation entry forces k = 1
+        assert lib.sprot_estimate_rotation(FAKE, FAKE, 1000, ctypes.byref(p), outs, None, None) == binding.E_INVAL
+
+
+@pytest.mark.parametrize("n", [0, -5, (1 << 31) + 1])
+def test_pair_counts_are_checked(libpath, n):
+    lib = binding.load(libpath)
+    p = binding.make_params()
+    out = binding.Rotation()
+    assert lib.sprot_estimate_rotation(FAKE, FAKE, n, ctypes.byref(p), ctypes.byref(out), None, None) == binding.E_INVAL
+
+
+def test_structural_argument_checks(libpath):
+    lib = binding.load(libpath)
+    p = binding.make_params()
+    out = binding.Rotation()
+    nf = ctypes.c_int32(0)
+    E = binding.E_INVAL
+    assert lib.sprot_estimate_rotation(FAKE, FAKE, 10, None, ctypes.byref(out), None, None) == E
+    assert lib.sprot_estimate_rotation(FAKE, FAKE, 10, ctypes.byref(p), None, None, None) == E
+    assert lib.sprot_estimate_rotation(None, FAKE, 10, ctypes.byref(p), ctypes.byref(out), None, None) == E
+    assert lib.sprot_estimate_rotation(FAKE, None, 10, ctypes.byref(p), ctypes.byref(out), None, None) == E
+    # host inputs cannot export device debug buffers
+    ph = binding.make_params(flags=binding.HOST_PTRS)
+    dbg = binding.Debug(None, None, None, None)
+    assert lib.sprot_estimate_rotations_ex(FAKE, FAKE, 10, ctypes.byref(ph), ctypes.byref(out), ctypes.byref(nf),
+                                           None, ctypes.byref(dbg), None) == E
+    # batches: empty, null, an instance with host pointers, an invalid instance after a valid one
+    assert lib.sprot_estimate_batch(None, 1, None) == E
+    inst = (binding.Instance * 2)()
+    assert lib.sprot_estimate_batch(inst, 0, None) == E
+    for i in range(2):
+        inst[i].P, inst[i].Q, inst[i].n = FAKE.value, FAKE.value, 100
+        inst[i].params = binding.make_params()
+        inst[i].out = ctypes.pointer(out)
+    inst[1].params.flags = binding.HOST_PTRS
+    assert lib.sprot_estimate_batch(inst, 2, None) == E
+    inst[1].params = binding.make_params(angle_bins=1)
+    assert lib.sprot_estimate_batch(inst, 2, None) == E
+    # stage entry points
+    assert lib.sprot_axis_vote(FAKE, FAKE, 10, 100, FAKE, None) == E            # G not a power of two
+    assert lib.sprot_axis_vote_sampled(FAKE, FAKE, 10, 64, 0, FAKE, None) == E  # J < 1
+    assert lib.sprot_axis_vote_sampled(FAKE, FAKE, 10, 64, 5000, FAKE, None) == E
+    assert lib.sprot_axis_vote_eps(FAKE, FAKE, 10, 64, -0.1, FAKE, None) == E  # eps < 0
+    assert lib.sprot_select_peaks(FAKE, 64, 0, 2.0, FAKE, FAKE, FAKE, None) == E  # k < 1
+
+
+def test_status_strings_and_defaults(libpath):
+    lib = binding.load(libpath)
+    codes = [binding.OK, binding.E_INVAL, binding.E_NOMEM, binding.E_CUDA, binding.E_TIMEOUT, binding.E_NOAXIS,
+             binding.E_UNIMPL, binding.E_BUSY]
+    texts = [lib.sprot_status_string(c).decode() for c in codes]
+    assert len(set(texts)) == len(codes) and all(texts)
+    p = binding.Params()
+    lib.sprot_default_params(ctypes.byref(p))
+    assert (p.grid, p.angle_bins, p.k, p.gate_window, p.angle_window, p.flags) == (256, 360, 1, 1, 1, 0)
+    assert abs(p.nms_deg - 2.0) < 1e-6 and abs(p.tau - 0.05) < 1e-12
+    assert [lib.sprot_autotune_grid(n) for n in (1, 2999, 3000, 299999, 300000, 10**7)] == [128, 128, 256, 256, 512, 512]
