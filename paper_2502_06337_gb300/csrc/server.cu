@@ -28,7 +28,7 @@ using Clock = std::chrono::steady_clock;
 // Worker threads (each its own stream and workspace) and the pairs one batch may hold: small
 // batches and several in flight keep a request's wait short when large requests arrive in a
 // row, at loads well below the device's throughput.
-constexpr int kServerWorkers = 4;
+constexpr int kServerWorkers = 12;
 constexpr int64_t kServerBatchPairs = 2 << 20;
 // initial input arena of a worker: a full batch of pairs (P and Q, 12 bytes each per pair)
 constexpr size_t kServerArenaBytes = (size_t)kServerBatchPairs * 24 + (64u << 10);
