@@ -65,14 +65,23 @@ def make_problem(
     sigma: float = 0.01,
     seed: int = 0,
     rotations=None,
+    unit: bool = False,
 ) -> Problem:
     """Draw P uniform in [-1,1]^3; for each rotation a, a share ``inlier_fracs[a]`` of the
     correspondences gets q = R_a p + N(0, sigma^2 I); the rest get q uniform in [-1,1]^3.
 
+    ``unit``: the recipe of the paper's synthetic experiments (Sec. V-A) instead: P and the
+    outlier points are unit-length vectors (normalised Gaussian draws); inliers are still
+    R_a p plus Gaussian noise of standard deviation sigma.
+
     Inlier positions are a random permutation, so inliers are not contiguous.
     """
     rng = _rng(seed)
-    P = rng.uniform(-1.0, 1.0, size=(n, 3))
+    if unit:
+        P = rng.standard_normal((n, 3))
+        P /= np.linalg.norm(P, axis=1, keepdims=True)
+    else:
+        P = rng.uniform(-1.0, 1.0, size=(n, 3))
     if rotations is None:
         rotations = [random_rotation(rng) for _ in inlier_fracs]
     counts = [int(round(f * n)) for f in inlier_fracs]
@@ -84,7 +93,11 @@ def make_problem(
     for a, c in enumerate(counts):
         truth[perm[start : start + c]] = a
         start += c
-    Q = rng.uniform(-1.0, 1.0, size=(n, 3))
+    if unit:
+        Q = rng.standard_normal((n, 3))
+        Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    else:
+        Q = rng.uniform(-1.0, 1.0, size=(n, 3))
     noise = rng.standard_normal((n, 3)) * sigma
     for a, R in enumerate(rotations):
         m = truth == a

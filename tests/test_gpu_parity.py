@@ -72,6 +72,20 @@ def test_small_workload_full_parity(lib, seed):
     print(rep)
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_unit_vector_recipe_full_parity(lib, seed):
+    """The paper's synthetic recipe (Sec. V-A: unit-length points and outliers, sigma 0.01) at
+    n = 1000 with half outliers: every stage against the oracle."""
+    prob = synth.make_problem(1000, (0.5,), 0.01, seed=200 + seed, unit=True)
+    G, J, tau = 256, 360, synth.default_tau(0.01)
+    g = parity.run_gpu(prob.P, prob.Q, G, J, tau=tau)
+    av = oracle.axis_vote(prob.P, prob.Q, G)
+    parity.check_solve(prob.P, prob.Q, g, G, J, tau=tau, av=av)
+    ref = oracle.solve(prob.P, prob.Q, G, J, tau=tau, grid=av["grid"])
+    assert oracle.rotation_error(ref["rotations"][0]["R"], g["rots"][0]["R"]) < parity.E2E_ROT_TOL
+    assert oracle.rotation_error(prob.rotations[0], g["rots"][0]["R"]) < math.radians(0.2)
+
+
 @pytest.mark.parametrize("n", [2, 50, 4099])
 def test_ragged_sizes_full_parity(lib, n):
     prob = synth.make_problem(n, (0.6,), 0.005, seed=100 + n)

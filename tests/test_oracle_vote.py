@@ -241,12 +241,14 @@ def test_kabsch_exact_recovery():
     assert np.allclose(oracle.kabsch(P, P @ R.T), R, atol=1e-13)
 
 
-def test_noise_free_solve_is_exact():
+@pytest.mark.parametrize("unit", [False, True])
+def test_noise_free_solve_is_exact(unit):
     """sigma = 0 with outliers: the refined rotation is R_gt to rounding when no outlier
-    lands within tau of R_gt p (checked; such seeds are skipped)."""
+    lands within tau of R_gt p (checked; such seeds are skipped). ``unit``: the paper's
+    unit-vector recipe (Sec. V-A) instead of points in the cube."""
     done = 0
     for seed in range(8):
-        prob = synth.make_problem(400, (0.6,), 0.0, seed=seed)
+        prob = synth.make_problem(400, (0.6,), 0.0, seed=seed, unit=unit)
         R = prob.rotations[0]
         res = np.linalg.norm(prob.Q.astype(np.float64) - prob.P @ R.T, axis=1)
         if np.any((prob.truth < 0) & (res <= 0.05)):
