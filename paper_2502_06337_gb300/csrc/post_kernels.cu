@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kStreamThreads)
   }
 }
 
-__device__ __noinline__ void kabsch_block(const InstDev& D, int a, int phase);
+__device__ __noinline__ void kabsch_all(const InstDev& D, int kf, int phase);
 
 // ---- FP64 sums of q p^T ----------------------------------------------------------------
 
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   block_sums(pq.acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
   // the last item of the instance solves the vote-set rotations
   if (D.done && last_block(&D.done[2], (uint32_t)D.n_items))
-    for (int a = 0; a < kf; ++a) kabsch_block(D, a, 0);
+    kabsch_all(D, kf, 0);
 }
 
 // Residual labels against every R_init (float32 test of ||q - R p||^2 <= tau^2) and the
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   block_sums(pq.acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
   // the last item of the instance solves the refined rotations
   if (D.done && last_block(&D.done[3], (uint32_t)D.n_items))
-    for (int a = 0; a < kf; ++a) kabsch_block(D, a, 1);
+    kabsch_all(D, kf, 1);
 }
 
 // ---- FP64 rotation from the sums (Horn's unit-quaternion method) --------------------------
@@ -881,10 +881,59 @@ __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
 // FP64 operation costs tens of cycles on this part, so the chains are kept short: the
 // singularity test needs no square root and X is M scaled by a power of two (the polar factor
 // does not depend on the scale).
-__device__ __noinline__ void kabsch_block(const InstDev& D, int a, int phase) {
+// The FP64 rotation of rotation a from its ten sums (M = sum q p^T and the count): the polar
+// factor of M (float32 start, FP64 refinement), with the Jacobi fallbacks for reflecting or
+// rank-deficient sums. One thread.
+__device__ void solve_rotation(const InstDev& D, int a, int phase, const double* tot) {
+  double s[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) s[t] = tot[t];
+  DevRot& R = D.rot[a];
+  double out[9];
+  const uint32_t cnt = (uint32_t)s[9];
+  if (cnt == 0) {
+    const double* fb = phase == 0 ? R.R_vote : R.R_init;
+    for (int t = 0; t < 9; ++t) out[t] = fb[t];
+  } else {
+    // det M > 1e-9 |M|_F^3 (polar path) tested as det > 0 and det^2 > 1e-18 (|M|_F^2)^3
+    const double c0 = s[4] * s[8] - s[5] * s[7], c1 = s[5] * s[6] - s[3] * s[8], c2 = s[3] * s[7] - s[4] * s[6];
+    const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
+    const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
+                      (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
+    // X = M 2^-e with the largest |entry| in [1, 2) (exact)
+    double mx = 0.0;
+    for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
+    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+    double X[9];
+    for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
+    double q[4];
+    const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
+                    polar_start_f32(X, q) && polar_refine_f64(X, q, out);
+    if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
+  }
+  if (phase == 0) {
+    for (int t = 0; t < 9; ++t) {
+      R.R_init[t] = out[t];
+      R.R_init_f[t] = (float)out[t];
+    }
+    R.n_vote_set = cnt;
+  } else {
+    for (int t = 0; t < 9; ++t) R.R[t] = out[t];
+    R.n_inliers = cnt;
+    R.n_degenerate = *D.n_deg;
+  }
+}
+
+// The sums of every rotation of an instance are reduced in turn by the whole block (a fixed
+// order); then the rotations' polar solves, each a single-thread FP64 dependency chain, run
+// concurrently, rotation a on lane 0 of warp a.
+static_assert(kStreamThreads / 32 >= kMaxK, "one warp per rotation");
+__device__ __noinline__ void kabsch_all(const InstDev& D, int kf, int phase) {
   __shared__ double part[kStreamThreads][10];
-  __shared__ double tot[10];
-  {
+  __shared__ double tot[kMaxK][10];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = 0; a < kf; ++a) {
     double v[10];
 #pragma unroll
     for (int t = 0; t < 10; ++t) v[t] = 0.0;
@@ -896,56 +945,16 @@ __device__ __noinline__ void kabsch_block(const InstDev& D, int a, int phase) {
     }
 #pragma unroll
     for (int t = 0; t < 10; ++t) part[threadIdx.x][t] = v[t];
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int col = w; col < 10; col += nw) {
-    double v = 0.0;
-    for (int i = l; i < (int)blockDim.x; i += 32) v += part[i][col];
-    v = warp_sum_d(v);
-    if (l == 0) tot[col] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s[10];
-#pragma unroll
-    for (int t = 0; t < 10; ++t) s[t] = tot[t];
-    DevRot& R = D.rot[a];
-    double out[9];
-    const uint32_t cnt = (uint32_t)s[9];
-    if (cnt == 0) {
-      const double* fb = phase == 0 ? R.R_vote : R.R_init;
-      for (int t = 0; t < 9; ++t) out[t] = fb[t];
-    } else {
-      // det M > 1e-9 |M|_F^3 (polar path) tested as det > 0 and det^2 > 1e-18 (|M|_F^2)^3
-      const double c0 = s[4] * s[8] - s[5] * s[7], c1 = s[5] * s[6] - s[3] * s[8], c2 = s[3] * s[7] - s[4] * s[6];
-      const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
-      const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
-                        (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
-      // X = M 2^-e with the largest |entry| in [1, 2) (exact)
-      double mx = 0.0;
-      for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
-      const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
-      const double sc = __longlong_as_double((long long)(1023 - e) << 52);
-      double X[9];
-      for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
-      double q[4];
-      const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
-                      polar_start_f32(X, q) && polar_refine_f64(X, q, out);
-      if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
+    __syncthreads();
+    for (int col = w; col < 10; col += nw) {
+      double x = 0.0;
+      for (int i = l; i < (int)blockDim.x; i += 32) x += part[i][col];
+      x = warp_sum_d(x);
+      if (l == 0) tot[a][col] = x;
     }
-    if (phase == 0) {
-      for (int t = 0; t < 9; ++t) {
-        R.R_init[t] = out[t];
-        R.R_init_f[t] = (float)out[t];
-      }
-      R.n_vote_set = cnt;
-    } else {
-      for (int t = 0; t < 9; ++t) R.R[t] = out[t];
-      R.n_inliers = cnt;
-      R.n_degenerate = *D.n_deg;
-    }
+    __syncthreads();
   }
+  if (l == 0 && w < kf) solve_rotation(D, w, phase, tot[w]);
   __syncthreads();
 }
 
