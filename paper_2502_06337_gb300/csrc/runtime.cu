@@ -292,6 +292,7 @@ Workspace* workspace_for(cudaStream_t st, int* status) {
   return slot.get();
 }
 
+
 // Pairs per work item of the per-pair kernels. One problem: about 600 items, so that the
 // problem alone fills the GPU. A batch: sized from the batch's total (the instances provide the
 // parallelism), so that small instances do not pay a block's fixed cost per few hundred pairs.
@@ -325,6 +326,22 @@ int tile_bytes(const InstPlan& ip) {
 }
 
 }  // namespace
+
+// Frees the workspace of stream st on the current device (its buffers, graphs, events and
+// second stream), for callers that destroy st; a later stream reusing the handle starts anew.
+void release_workspace(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::unique_ptr<Workspace> w;
+  {
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    auto it = g_ws.find({dev, st});
+    if (it == g_ws.end()) return;
+    w = std::move(it->second);
+    g_ws.erase(it);
+  }
+  // destroyed here, outside the lock
+}
 
 size_t problem_footprint(int64_t n, int G, int J, int k) {
   int T = 0;

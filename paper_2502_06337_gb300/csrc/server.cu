@@ -174,6 +174,7 @@ void sprot_server::worker_main(int idx) {
   }
   if (arena) cudaFreeAsync(arena, st);
   cudaStreamSynchronize(st);
+  release_workspace(st);  // the worker's workspace goes with its stream
   cudaStreamDestroy(st);
 }
 

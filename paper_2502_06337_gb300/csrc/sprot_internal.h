@@ -102,6 +102,9 @@ struct Problem {
 // graphs: replay the launch sequence from a CUDA graph when its shape repeats (see runtime.cu)
 int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true);
 
+// Frees the solve() workspace of stream st (call before destroying st).
+void release_workspace(cudaStream_t st);
+
 // Device bytes one problem occupies in a solve() workspace (inputs excluded).
 size_t problem_footprint(int64_t n, int G, int J, int k);
 

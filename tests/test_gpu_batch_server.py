@@ -260,3 +260,28 @@ def test_batch_with_a_headline_instance_and_labels(lib):
         alone = B.estimate_rotations(P, Q, alone_prm, labels=lab_alone)
         _same(res[i], alone)
         assert torch.equal(labs[i], lab_alone)
+
+
+def test_server_cycles_release_device_memory(lib):
+    """Creating, using and destroying servers repeatedly does not accumulate device memory:
+    each worker's workspace and input arena are freed with its stream."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    prob = synth.make_problem(200_000, (0.2,), 0.01, seed=95)
+    prm = B.make_params(grid=0, tau=0.05)
+
+    def cycle():
+        with B.Server(4 << 30, max_batch=8) as srv:
+            tickets = [srv.submit(prob.P, prob.Q, prm) for _ in range(24)]
+            assert all(srv.wait(t)["status"] == 0 for t in tickets)
+
+    cycle()  # the first cycle loads modules and grows the memory pools
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        cycle()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < (256 << 20), f"{(free0 - free1) / 2**20:.0f} MiB not returned"
