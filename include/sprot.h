@@ -35,7 +35,8 @@
  *   - Return value: SPROT_OK (0) or a negative status; sprot_status_string() describes it.
  *     On error nothing is written to the outputs except where stated.
  *   - The library allocates its own device workspace (cached per device and stream, grown on
- *     demand); sprot_release_workspaces() frees it.
+ *     demand); sprot_release_workspaces() frees all of them, and
+ *     sprot_release_stream_workspace() the one of a stream that is about to be destroyed.
  */
 #ifndef SPROT_H
 #define SPROT_H
@@ -282,6 +283,12 @@ int sprot_server_destroy(sprot_server* s);
 
 /* Frees every cached device workspace of the calling process (device memory returned). */
 void sprot_release_workspaces(void);
+
+/* Frees the cached workspace of one stream on the current device (its buffers, captured
+ * graphs and events), waiting for the work it holds. Call it before destroying a stream that
+ * was passed to the library; a later stream that reuses the handle starts afresh. No effect
+ * when the stream has no workspace. */
+void sprot_release_stream_workspace(void* stream);
 
 /* Number of kernels this library has launched in the process (monotone counter). */
 uint64_t sprot_kernel_launch_count(void);

@@ -26,7 +26,7 @@ EXPORTS = [
     "sprot_axis_vote_sampled", "sprot_axis_vote_eps", "sprot_refine_axis",
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
-    "sprot_release_workspaces", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
+    "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
     "sprot_kernel_timing", "sprot_kernel_timing_read",
 ]
 
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     lib.sprot_server_destroy.argtypes = [vp]
     lib.sprot_release_workspaces.argtypes = []
     lib.sprot_release_workspaces.restype = None
+    lib.sprot_release_stream_workspace.argtypes = [vp]
+    lib.sprot_release_stream_workspace.restype = None
     lib.sprot_kernel_launch_count.argtypes = []
     lib.sprot_kernel_launch_count.restype = C.c_uint64
     lib.sprot_probe_smem_atomic_rate.argtypes = [i32, C.POINTER(C.c_double), vp]
@@ -449,3 +451,9 @@ def kernel_timing_read():
 
 def release_workspaces():
     load().sprot_release_workspaces()
+
+
+def release_stream_workspace(stream=None):
+    """Frees the library's workspace of ``stream`` (default: the current torch stream); call
+    before the stream is destroyed."""
+    load().sprot_release_stream_workspace(_stream(stream))

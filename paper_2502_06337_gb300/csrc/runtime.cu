@@ -960,6 +960,8 @@ int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream) {
   return st;
 }
 
+void sprot_release_stream_workspace(void* stream) { release_workspace(reinterpret_cast<cudaStream_t>(stream)); }
+
 void sprot_release_workspaces(void) {
   std::lock_guard<std::mutex> g(g_ws_mu);
   g_ws.clear();
