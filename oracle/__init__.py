@@ -33,6 +33,7 @@ from .vote import (  # noqa: F401
     axis_vote,
     cell_votes,
     peak_cell,
+    local_maxima,
     top_k_cells,
     window_gate,
     pair_angles,

@@ -169,23 +169,56 @@ def axis_angle_deg(r1, r2) -> float:
     return math.degrees(math.acos(min(1.0, c)))
 
 
+def local_maxima(grid):
+    """Cells that are peaks of the accumulator: strict local maxima of the key
+    (count, -row-major index) over their 8 neighbours (clipped to the grid).
+
+    Reading (Sec. IV-D and Fig. 3d-f detect the rotation axes as the peaks of the 2-D
+    histogram but give no definition): a cell is a peak when no neighbour has more votes,
+    and among equal counts the smallest index wins, so a plateau resolves to a definite cell
+    and a cell on the flank of a larger peak (a shoulder) is never a peak. Returns a
+    boolean G x G mask."""
+    grid = np.asarray(grid)
+    G0, G1 = grid.shape
+    idx = np.arange(G0 * G1).reshape(G0, G1)
+    peak = np.ones((G0, G1), dtype=bool)
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            if dr == 0 and dc == 0:
+                continue
+            # the cell (r, c) against its neighbour (r + dr, c + dc), where it exists
+            r0, r1 = max(0, -dr), G0 - max(0, dr)
+            c0, c1 = max(0, -dc), G1 - max(0, dc)
+            here = grid[r0:r1, c0:c1]
+            there = grid[r0 + dr:r1 + dr, c0 + dc:c1 + dc]
+            here_i = idx[r0:r1, c0:c1]
+            there_i = idx[r0 + dr:r1 + dr, c0 + dc:c1 + dc]
+            beaten = (there > here) | ((there == here) & (there_i < here_i))
+            peak[r0:r1, c0:c1] &= ~beaten
+    return peak
+
+
 def top_k_cells(grid, k: int, nms_deg: float):
     """Several rotation axes from one accumulator (Sec. IV-D; Fig. 3d-f).
 
-    Reading (the paper states no rule for separating peaks): greedy non-maximum
-    suppression. Cells are visited by (count descending, row-major index ascending); a cell
-    becomes a peak if its count is positive and its axis is more than ``nms_deg`` degrees
-    from every peak taken so far. Stops after k peaks. With k = 1 this is ``peak_cell``.
-    Returns a list of (row, col, count)."""
+    Reading: the candidates are the accumulator's peaks (``local_maxima``); the paper
+    states no rule for separating them, so a greedy non-maximum suppression is applied.
+    Peaks are visited by (count descending, row-major index ascending); a peak is taken if
+    its count is positive and its axis is more than ``nms_deg`` degrees from every axis
+    taken so far. Stops after k peaks. The global maximum is always a peak, so with k = 1
+    this is ``peak_cell``. Returns a list of (row, col, count)."""
     grid = np.asarray(grid)
     G = grid.shape[1]
     flat = grid.ravel()
+    is_peak = local_maxima(grid).ravel()
     order = np.lexsort((np.arange(flat.size), -flat))
     peaks, axes = [], []
     for idx in order:
         cnt = int(flat[idx])
         if cnt <= 0 or len(peaks) >= k:
             break
+        if not is_peak[idx]:
+            continue
         row, col = divmod(int(idx), G)
         r = cell_axis(G, row, col)
         if any(axis_angle_deg(r, a) <= nms_deg for a in axes):

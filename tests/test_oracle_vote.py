@@ -146,8 +146,61 @@ def test_top_k_suppression_by_construction():
     g[200, 20] = 60    # peak 3
     peaks = oracle.top_k_cells(g, 3, 2.0)
     assert peaks == [(128, 128, 100), (40, 200, 70), (200, 20, 60)]
-    assert oracle.top_k_cells(g, 3, 0.0) == [(128, 128, 100), (128, 129, 90), (129, 128, 80)]
+    # without suppression the neighbours of a peak are still no peaks of their own
+    assert oracle.top_k_cells(g, 3, 0.0) == [(128, 128, 100), (40, 200, 70), (200, 20, 60)]
     assert oracle.top_k_cells(np.zeros((8, 8), dtype=np.int64), 2, 2.0) == []
+
+
+def _local_maxima_by_loops(g):
+    """Peaks by their definition, one cell at a time: no neighbour (8-neighbourhood, inside
+    the grid) has a larger count, or an equal count at a smaller row-major index."""
+    G0, G1 = g.shape
+    out = np.zeros(g.shape, dtype=bool)
+    for r in range(G0):
+        for c in range(G1):
+            ok = True
+            for rr in range(r - 1, r + 2):
+                for cc in range(c - 1, c + 2):
+                    if (rr, cc) == (r, c) or not (0 <= rr < G0 and 0 <= cc < G1):
+                        continue
+                    if g[rr, cc] > g[r, c] or (g[rr, cc] == g[r, c] and rr * G1 + cc < r * G1 + c):
+                        ok = False
+            out[r, c] = ok
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_local_maxima_brute_force(seed):
+    """The shifted-array form of the peak test equals the cell-by-cell definition, on small
+    grids with many ties (counts 0-3) so that plateaus and grid borders are exercised."""
+    rng = np.random.default_rng(seed)
+    g = rng.integers(0, 4, size=(9, 9)).astype(np.int64)
+    assert np.array_equal(oracle.local_maxima(g), _local_maxima_by_loops(g))
+
+
+def test_local_maxima_plateau_and_border():
+    g = np.zeros((6, 6), dtype=np.int64)
+    g[2, 2] = g[2, 3] = 7  # a two-cell plateau: the smaller index is the peak
+    g[5, 5] = 3            # a corner cell with lower neighbours
+    m = oracle.local_maxima(g)
+    assert m[2, 2] and not m[2, 3] and m[5, 5]
+    # zero cells away from the plateau are peaks of the key too (their count is 0, never taken)
+    assert oracle.top_k_cells(g, 5, 0.0) == [(2, 2, 7), (5, 5, 3)]
+
+
+def test_top_k_skips_the_shoulder_of_a_larger_peak():
+    """A cell on the flank of a large peak, outside the suppression radius, outranks a
+    smaller peak of its own; the flank cell is no peak (Sec. IV-D takes the axes at the
+    accumulator's peaks), so the smaller peak is the second axis."""
+    G = 256  # near the centre a cell spans about 0.9 degrees, so 3 cells lie beyond 2 degrees
+    g = np.zeros((G, G), dtype=np.int64)
+    for dc, cnt in enumerate([100, 90, 75, 60, 45, 30]):
+        g[128, 128 + dc] = cnt  # peak and its descending flank
+    g[40, 200] = 50             # a separate, smaller peak
+    assert oracle.top_k_cells(g, 2, 2.0) == [(128, 128, 100), (40, 200, 50)]
+    # the flank cell 3 columns out is beyond the radius, but it is not a peak
+    assert ov.axis_angle_deg(oracle.cell_axis(G, 128, 128), oracle.cell_axis(G, 128, 131)) > 2.0
+    assert not oracle.local_maxima(g)[128, 131]
 
 
 def test_top_k_suppresses_antipodal_axis():
