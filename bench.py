@@ -314,10 +314,6 @@ def run_sprot(args):
             except Exception as e:
                 out["multi_rotation"] = {"error": repr(e)}
             try:
-                out["small_two_rotations"] = run_small_two(B, dev)
-            except Exception as e:
-                out["small_two_rotations"] = {"error": repr(e)}
-            try:
                 out["paper_recipe"] = run_paper_recipe(B, dev)
             except Exception as e:
                 out["paper_recipe"] = {"error": repr(e)}
@@ -491,35 +487,6 @@ def run_multi(B, dev, reps=10):
     return {"workload": "n=2e5, 3 x 15% inliers, 55% outliers, sigma=0.01, 512x512, 720 bins, k=3, NMS 2 deg",
             "ms": ms, "Mcorr_per_s": prob.n / ms / 1e3, "found": len(rots),
             "rot_err_deg_vs_truth": errs}
-
-
-def run_small_two(B, dev, reps=50):
-    """A problem shaped like the scenes of the paper's multi-model experiment (Table 4: about
-    300 correspondences, two rotations): n = 300, 2 x 40 % inliers, sigma 0.01, the autotuned
-    grid (128^2), 360 bins, k = 2. Latency of one solve (device-resident inputs) and each true
-    rotation's error."""
-    import torch
-
-    from paper_2502_06337_gb300 import synth
-
-    errs_all, ms_all = [], []
-    for seed in range(10):
-        prob = synth.make_problem(300, (0.4, 0.4), 0.01, seed=300 + seed)
-        P = torch.from_numpy(prob.P).to(dev)
-        Q = torch.from_numpy(prob.Q).to(dev)
-        prm = B.make_params(grid=0, angle_bins=360, k=2, nms_deg=2.0, tau=synth.default_tau(0.01))
-        for _ in range(3):
-            rots = B.estimate_rotations(P, Q, prm, allow_noaxis=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            rots = B.estimate_rotations(P, Q, prm, allow_noaxis=True)
-        ms_all.append((time.perf_counter() - t0) * 1e3 / reps)
-        errs_all += [min([math.degrees(_rot_err(Rg, r["R"])) for r in rots] or [180.0]) for Rg in prob.rotations]
-    return {"workload": "10 scenes of n=300, 2 x 40% inliers, sigma=0.01, 128x128 (autotuned), 360 bins, k=2",
-            "ms_per_solve_wall": float(np.median(ms_all)), "median_rot_err_deg": float(np.median(errs_all)),
-            "max_rot_err_deg": float(np.max(errs_all)),
-            "paper": {"s": 0.01, "avg_rot_err_deg": 0.2037, "data": "10 real scenes of about 300 matches"}}
 
 
 def run_paper_recipe(B, dev, reps=10):

@@ -187,7 +187,7 @@ int sprot_axis_vote_eps(const float* P, const float* Q, int64_t n, int32_t grid_
  * refines the cell-resolution axis. P, Q, labels: device pointers. hint: host double[3] or
  * NULL; r is signed so that r . hint >= 0, else r_z <= 0. axis: host double[3];
  * lambda_min (the smallest eigenvalue, the residual sum of squares) and count (pairs used):
- * host, may be NULL. Synchronous. Errors: E_INVAL, E_NOAXIS (fewer than two independent
+ * host, may be NULL. Nothing is written on error. Synchronous. Errors: E_INVAL, E_NOAXIS (fewer than two independent
  * directions: the axis is not determined), E_NOMEM, E_CUDA. */
 int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* labels,
                       int32_t label, const double* hint, double* axis, double* lambda_min,
@@ -281,13 +281,16 @@ int sprot_server_destroy(sprot_server* s);
 
 /* ---- housekeeping and measurement ----------------------------------------------------------- */
 
-/* Frees every cached device workspace of the calling process (device memory returned). */
+/* Frees every cached device workspace of the calling process (device memory returned). A
+ * workspace that a call on another host thread is using at that moment stays alive until that
+ * call returns, and is freed then; the next call on that stream starts a new workspace. */
 void sprot_release_workspaces(void);
 
 /* Frees the cached workspace of one stream on the current device (its buffers, captured
  * graphs and events), waiting for the work it holds. Call it before destroying a stream that
  * was passed to the library; a later stream that reuses the handle starts afresh. No effect
- * when the stream has no workspace. */
+ * when the stream has no workspace. A call still running on the stream in another host
+ * thread keeps the workspace until it returns. */
 void sprot_release_stream_workspace(void* stream);
 
 /* Number of kernels this library has launched in the process (monotone counter). */

@@ -191,6 +191,24 @@ __global__ void __launch_bounds__(kReduceWords / 4)
     finalize_instance(D);
 }
 
+// A peak of the accumulator (Sec. IV-D; Fig. 3d-f): no cell of the 8-neighbourhood (inside
+// the grid) has a larger key, i.e. more votes, or as many at a smaller row-major index.
+__device__ __forceinline__ bool is_peak(const uint32_t* __restrict__ grid, int G, int row, int col,
+                                        unsigned long long key) {
+  for (int dr = -1; dr <= 1; ++dr) {
+    const int rr = row + dr;
+    if (rr < 0 || rr >= G) continue;
+    for (int dc = -1; dc <= 1; ++dc) {
+      const int cc = col + dc;
+      if ((dr == 0 && dc == 0) || cc < 0 || cc >= G) continue;
+      if (peak_key(grid[(int64_t)rr * G + cc], (uint32_t)(rr * G + cc)) > key) return false;
+    }
+  }
+  return true;
+}
+
+// Round `round` of the greedy top-k: the largest peak whose axis line is farther than the
+// suppression radius from every axis taken in the earlier rounds.
 __global__ void __launch_bounds__(256)
     k_nms_round(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts, int round) {
   const ReduceItem I = items[blockIdx.x];
@@ -223,7 +241,7 @@ __global__ void __launch_bounds__(256)
       CellAxis ca = cell_axis(G, row, col);
       bool sup = false;
       for (int t = 0; t < round; ++t) sup |= suppressed(ca, taken[t], D.cos_nms);
-      if (!sup) best = key;
+      if (!sup && is_peak(D.grid, G, row, col, key)) best = key;
     }
   }
   best = block_max_u64(best);
@@ -634,47 +652,57 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
 
 // ---- FP64 rotation from the sums (Horn's unit-quaternion method) --------------------------
 
-// Eigen-decomposition of a symmetric 4x4 matrix by cyclic Jacobi rotations; returns the unit
-// eigenvector of the largest eigenvalue in v.
-__device__ void jacobi4_top(double A[4][4], double v[4]) {
-  double V[4][4];
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+// Eigen-decomposition of a symmetric N x N matrix by cyclic Jacobi rotations (each rotation
+// zeroes one off-diagonal entry; the sweeps converge quadratically). On return A is diagonal
+// to working precision (the eigenvalues on the diagonal) and the columns of V are the unit
+// eigenvectors.
+template <int N>
+__device__ void jacobi_sym(double (&A)[N][N], double (&V)[N][N]) {
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 24; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
         tot += A[i][j] * A[i][j];
         if (i != j) off += A[i][j] * A[i][j];
       }
     if (off <= 1e-28 * tot || off == 0.0) break;
-    for (int p = 0; p < 3; ++p)
-      for (int q = p + 1; q < 4; ++q) {
+    for (int p = 0; p < N - 1; ++p)
+      for (int q = p + 1; q < N; ++q) {
         double apq = A[p][q];
         if (apq == 0.0) continue;
         double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
         double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
         double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < 4; ++k) {  // A <- A J
+        for (int k = 0; k < N; ++k) {  // A <- A J
           double akp = A[k][p], akq = A[k][q];
           A[k][p] = c * akp - s * akq;
           A[k][q] = s * akp + c * akq;
         }
-        for (int k = 0; k < 4; ++k) {  // A <- J^T A
+        for (int k = 0; k < N; ++k) {  // A <- J^T A
           double apk = A[p][k], aqk = A[q][k];
           A[p][k] = c * apk - s * aqk;
           A[q][k] = s * apk + c * aqk;
         }
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < N; ++k) {
           double vkp = V[k][p], vkq = V[k][q];
           V[k][p] = c * vkp - s * vkq;
           V[k][q] = s * vkp + c * vkq;
         }
       }
   }
+}
+
+// The unit eigenvector of the largest eigenvalue of a symmetric 4x4 matrix.
+__device__ void jacobi4_top(double A[4][4], double v[4]) {
+  double M[4][4], V[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) M[i][j] = A[i][j];
+  jacobi_sym<4>(M, V);
   int best = 0;
   for (int i = 1; i < 4; ++i)
-    if (A[i][i] > A[best][best]) best = i;
+    if (M[i][i] > M[best][best]) best = i;
   double n = 0.0;
   for (int i = 0; i < 4; ++i) n += V[i][best] * V[i][best];
   n = sqrt(n);
@@ -1031,10 +1059,10 @@ __global__ void __launch_bounds__(kAxisThreads)
   }
 }
 
-// Sum of the partials (fixed order) and the eigenvector of S for its smallest eigenvalue by
-// power iteration on adj(S): adj(S) has the eigenvalues lambda_j lambda_k (pairs of S's), the
-// largest belonging to S's smallest eigenvector, and converges at the rate lambda_min /
-// lambda_mid from its largest column. out = axis[3], lambda_min, count, status.
+// Sum of the partials (fixed order) and the eigenvector of S for its smallest eigenvalue, by
+// cyclic Jacobi rotations in FP64 (converged to working precision whatever the eigen-gap).
+// The axis is undetermined when S has rank <= 1 (adj(S) vanishes relative to trace(S)^2).
+// out = axis[3], lambda_min, count, status.
 __global__ void __launch_bounds__(kAxisThreads)
     k_axis_eig(const double* __restrict__ partial, int nb, double h0, double h1, double h2, int has_hint,
                double* __restrict__ out) {
@@ -1063,41 +1091,21 @@ __global__ void __launch_bounds__(kAxisThreads)
   const double A[9] = {s11 * s22 - s12 * s12, s02 * s12 - s01 * s22, s01 * s12 - s02 * s11,
                        s02 * s12 - s01 * s22, s00 * s22 - s02 * s02, s01 * s02 - s00 * s12,
                        s01 * s12 - s02 * s11, s01 * s02 - s00 * s12, s00 * s11 - s01 * s01};
-  double best = -1.0, x[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; k < 3; ++k) {
-    const double nk = A[k] * A[k] + A[3 + k] * A[3 + k] + A[6 + k] * A[6 + k];
-    if (nk > best) {
-      best = nk;
-      x[0] = A[k];
-      x[1] = A[3 + k];
-      x[2] = A[6 + k];
-    }
-  }
+  double best = 0.0;
+  for (int k = 0; k < 3; ++k) best = fmax(best, A[k] * A[k] + A[3 + k] * A[3 + k] + A[6 + k] * A[6 + k]);
   const double tr = s00 + s11 + s22;
   // fewer than two independent directions: adj(S) vanishes (relative to trace(S)^2)
   if (!(best > 1e-24 * (tr * tr) * (tr * tr))) {
     out[5] = (double)SPROT_E_NOAXIS;
     return;
   }
-  for (int it = 0; it < 64; ++it) {
-    // exact power-of-two rescaling keeps x in range
-    const double mx = fmax(fabs(x[0]), fmax(fabs(x[1]), fabs(x[2])));
-    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
-    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
-    const double y0 = x[0] * sc, y1 = x[1] * sc, y2 = x[2] * sc;
-    const double n0 = A[0] * y0 + A[1] * y1 + A[2] * y2;
-    const double n1 = A[3] * y0 + A[4] * y1 + A[5] * y2;
-    const double n2 = A[6] * y0 + A[7] * y1 + A[8] * y2;
-    // change of direction: |x_new/|x_new| - x_old/|x_old||^2 via the cosine
-    const double nn = n0 * n0 + n1 * n1 + n2 * n2, yy = y0 * y0 + y1 * y1 + y2 * y2;
-    const double dot = n0 * y0 + n1 * y1 + n2 * y2;
-    x[0] = n0;
-    x[1] = n1;
-    x[2] = n2;
-    if (dot > 0.0 && 1.0 - dot * dot / (nn * yy) < 1e-30) break;
-  }
-  const double rn = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-  double r0 = x[0] * rn, r1 = x[1] * rn, r2 = x[2] * rn;
+  double E[3][3] = {{s00, s01, s02}, {s01, s11, s12}, {s02, s12, s22}}, V[3][3];
+  jacobi_sym<3>(E, V);
+  int lo = 0;
+  for (int k = 1; k < 3; ++k)
+    if (E[k][k] < E[lo][lo]) lo = k;
+  const double rn = 1.0 / sqrt(V[0][lo] * V[0][lo] + V[1][lo] * V[1][lo] + V[2][lo] * V[2][lo]);
+  double r0 = V[0][lo] * rn, r1 = V[1][lo] * rn, r2 = V[2][lo] * rn;
   bool flip;
   if (has_hint) {
     flip = r0 * h0 + r1 * h1 + r2 * h2 < 0.0;

@@ -273,9 +273,12 @@ struct Workspace {
 };
 
 std::mutex g_ws_mu;
-std::map<std::pair<int, cudaStream_t>, std::unique_ptr<Workspace>> g_ws;
+// Workspaces are shared: a call holds its own reference for its whole duration, so releasing
+// the cache (sprot_release_workspaces / sprot_release_stream_workspace) while a call runs on
+// another host thread frees that workspace only when the call returns.
+std::map<std::pair<int, cudaStream_t>, std::shared_ptr<Workspace>> g_ws;
 
-Workspace* workspace_for(cudaStream_t st, int* status) {
+std::shared_ptr<Workspace> workspace_for(cudaStream_t st, int* status) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     *status = SPROT_E_CUDA;
@@ -289,7 +292,7 @@ Workspace* workspace_for(cudaStream_t st, int* status) {
     slot->stream = st;
   }
   *status = SPROT_OK;
-  return slot.get();
+  return slot;
 }
 
 
@@ -332,7 +335,7 @@ int tile_bytes(const InstPlan& ip) {
 void release_workspace(cudaStream_t st) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
-  std::unique_ptr<Workspace> w;
+  std::shared_ptr<Workspace> w;
   {
     std::lock_guard<std::mutex> g(g_ws_mu);
     auto it = g_ws.find({dev, st});
@@ -340,7 +343,8 @@ void release_workspace(cudaStream_t st) {
     w = std::move(it->second);
     g_ws.erase(it);
   }
-  // destroyed here, outside the lock
+  // destroyed here, outside the lock, unless a call in flight still holds it (then when that
+  // call returns)
 }
 
 size_t problem_footprint(int64_t n, int G, int J, int k) {
@@ -403,7 +407,7 @@ bool run_graph(Workspace* ws, const std::vector<uint64_t>& key, cudaStream_t st,
 int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   const int m = (int)probs.size();
   int status = SPROT_OK;
-  Workspace* ws = workspace_for(st, &status);
+  std::shared_ptr<Workspace> ws = workspace_for(st, &status);
   if (!ws) return status;
   std::lock_guard<std::mutex> lock(ws->mu);
   const int nsm = sm_count(ws->device);
@@ -658,7 +662,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
                          (uint64_t)plan[i].o_mask, (uint64_t)plan[i].o_labels})
         k2.push_back(v);
     }
-    ok = run_graph(ws, k2, st, [&] { return enqueue(false); });
+    ok = run_graph(ws.get(), k2, st, [&] { return enqueue(false); });
   }
   if (!ok || !ck(cudaStreamSynchronize(st))) return SPROT_E_CUDA;
   if (vt) {
@@ -709,7 +713,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
 int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* grid,
                    cudaStream_t st, float eps) {
   int status = SPROT_OK;
-  Workspace* ws = workspace_for(st, &status);
+  std::shared_ptr<Workspace> ws = workspace_for(st, &status);
   if (!ws) return status;
   std::lock_guard<std::mutex> lock(ws->mu);
   const int nsm = sm_count(ws->device);
@@ -777,7 +781,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
 int select_peaks(const uint32_t* grid, int G, int k, float nms_deg, int32_t* cells,
                  uint32_t* counts, int32_t* n_found, cudaStream_t st) {
   int status = SPROT_OK;
-  Workspace* ws = workspace_for(st, &status);
+  std::shared_ptr<Workspace> ws = workspace_for(st, &status);
   if (!ws) return status;
   std::lock_guard<std::mutex> lock(ws->mu);
   std::vector<ReduceItem> rit;
@@ -902,7 +906,7 @@ int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* 
   if (!P || !Q || !axis || n < 1 || n > (int64_t)1 << 31) return SPROT_E_INVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int status = SPROT_OK;
-  Workspace* ws = workspace_for(st, &status);
+  std::shared_ptr<Workspace> ws = workspace_for(st, &status);
   if (!ws) return status;
   std::lock_guard<std::mutex> lock(ws->mu);
   const int chunk = kStreamChunk;
@@ -918,11 +922,11 @@ int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* 
   if (cudaMemcpyAsync(hout, dout, sizeof(double) * 6, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SPROT_E_CUDA;
-  if (count) *count = (int64_t)hout[4];
   const int res = (int)hout[5];
   if (res != SPROT_OK) return res;
   for (int t = 0; t < 3; ++t) axis[t] = hout[t];
   if (lambda_min) *lambda_min = hout[3];
+  if (count) *count = (int64_t)hout[4];
   return SPROT_OK;
 }
 
@@ -963,8 +967,12 @@ int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream) {
 void sprot_release_stream_workspace(void* stream) { release_workspace(reinterpret_cast<cudaStream_t>(stream)); }
 
 void sprot_release_workspaces(void) {
-  std::lock_guard<std::mutex> g(g_ws_mu);
-  g_ws.clear();
+  std::map<std::pair<int, cudaStream_t>, std::shared_ptr<Workspace>> gone;
+  {
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    gone.swap(g_ws);
+  }
+  // freed here, outside the lock (a workspace still held by a call in flight: when it returns)
 }
 
 uint64_t sprot_kernel_launch_count(void) { return g_launches.load(); }

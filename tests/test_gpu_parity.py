@@ -311,11 +311,11 @@ def test_multi_rotation_at_full_size(lib):
     assert np.all(got[lo == hi] == cnt[lo == hi])
     parity.check_solve(prob.P, prob.Q, g, G, J, k=k, nms=nms, tau=tau)
     # Accuracy (not parity): with sigma = 0.01 a rotation of small angle leaves a low, broad
-    # peak; the greedy top 3 with a 2 degree radius can take a shoulder of a sharper peak
-    # instead (seed 3: the 22 and 26 degree rotations peak at 3898 and 3611 votes, the 85
-    # degree one at 11108 with a 3894-vote shoulder 2.1 degrees away). Two of three are found.
+    # peak (seed 3: the 22 and 26 degree rotations peak at 3898 and 3631 votes, the 85 degree
+    # one at 11108 with a 3894-vote cell on its flank 2.1 degrees away). Only peaks of the
+    # accumulator compete for the top 3, so all three rotations are found.
     errs = sorted(min(oracle.rotation_error(Rg, r["R"]) for r in g["rots"]) for Rg in prob.rotations)
-    assert errs[1] < math.radians(0.5)
+    assert errs[2] < math.radians(0.5)
 
 
 @pytest.mark.parametrize("G,n", [(1024, 60), (2048, 12)])
