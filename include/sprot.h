@@ -74,6 +74,7 @@ extern "C" {
 #define SPROT_MAX_GRID 2048
 #define SPROT_MAX_ANGLE_BINS 4096
 #define SPROT_MAX_SAMPLES 4096     /* points per circle of the sampled accumulator */
+#define SPROT_MAX_BANDS 48         /* row bands of one accumulator in the axis vote */
 
 /* Solver parameters. The paper fixes none of them; the defaults are those of
  * sprot_default_params(). */
@@ -169,6 +170,15 @@ int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n,
  * overwritten, not accumulated. Errors: E_INVAL (NULL, n < 1, bad G), E_NOMEM, E_CUDA. */
 int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size,
                     uint32_t* grid, void* stream);
+
+/* The work split of the axis vote (Algorithm 1's accumulator) for n pairs on a G x G grid on
+ * the current device, as a single solve (batched = 0) or a batch instance (batched = 1) would
+ * use it: the accumulator is cut into *n_bands row bands, band b covering rows
+ * [band_row0[b], band_row0[b+1]) (band_row0: host int32[SPROT_MAX_BANDS + 1]), and the pairs
+ * into *slices consecutive slices of at most 65535 circles. Host-only; for tests and tuning.
+ * Errors: E_INVAL (NULL, n < 1, bad G), E_CUDA (no device). */
+int sprot_vote_plan(int64_t n, int32_t grid_size, int32_t batched, int32_t* n_bands,
+                    int32_t* band_row0, int32_t* slices);
 
 /* The consensus accumulator of Eq. 9 at cell resolution: grid[G*G] (device uint32) = the
  * number of non-degenerate pairs for which some axis r of the closed cell has

@@ -32,6 +32,7 @@ from .vote import (  # noqa: F401
     circle_cell_extrema,
     axis_vote,
     cell_votes,
+    row_votes,
     peak_cell,
     local_maxima,
     top_k_cells,

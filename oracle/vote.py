@@ -150,6 +150,28 @@ def cell_votes(P, Q, G: int, rows, cols):
     return out[0], out[1], out[2]
 
 
+def row_votes(P, Q, G: int, row: int, chunk: int = 8192):
+    """Votes of every cell of one row over all circles (the same closed-cell test as
+    ``axis_vote``, evaluated for one row at a time, in chunks of circles, so that whole rows
+    of a 10^6-circle accumulator can be checked). Returns (count, lo, hi), each of length G."""
+    D, deg = _differences(P, Q)
+    e = grid_edges(G)
+    out = np.zeros((3, G), dtype=np.int64)
+    for a in range(0, len(D), chunk):
+        d = D[a:a + chunk][~deg[a:a + chunk]]
+        nrm = np.sqrt(np.einsum("ij,ij->i", d, d))[:, None]
+        hmin, hmax = _quadratic_range(d[:, 2], 2.0 * d[:, 1], e[row], e[row + 1])
+        gmin, gmax = _quadratic_range(d[:, 2][:, None], 2.0 * d[:, 0][:, None], e[None, :-1], e[None, 1:])
+        Fmin = gmin + (hmin - d[:, 2])[:, None]
+        Fmax = gmax + (hmax - d[:, 2])[:, None]
+        voted = (Fmin <= 0.0) & (Fmax >= 0.0)
+        flag = (np.abs(Fmin) <= BAND * nrm) | (np.abs(Fmax) <= BAND * nrm)
+        out[0] += voted.sum(axis=0)
+        out[1] += (voted & ~flag).sum(axis=0)
+        out[2] += (voted | flag).sum(axis=0)
+    return out[0], out[1], out[2]
+
+
 # ---------------------------------------------------------------------------------------
 # Peaks (Algorithm 1; Sec. IV-A; multi-rotation Sec. IV-D)
 # ---------------------------------------------------------------------------------------

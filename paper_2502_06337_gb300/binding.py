@@ -19,6 +19,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOAXIS, E_UNIMPL, E_BUSY = 0, -1, -2,
 HOST_PTRS = 0x1
 SUBCELL_AXIS = 0x2
 MAX_K = 8
+MAX_BANDS = 48
 
 EXPORTS = [
     "sprot_default_params", "sprot_status_string", "sprot_estimate_rotation",
@@ -27,7 +28,7 @@ EXPORTS = [
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
-    "sprot_kernel_timing", "sprot_kernel_timing_read",
+    "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan",
 ]
 
 
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_axis_vote.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.sprot_axis_vote_sampled.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.sprot_axis_vote_eps.argtypes = [vp, vp, i64, i32, C.c_float, vp, vp]
+    lib.sprot_vote_plan.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.sprot_refine_axis.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i64), vp]
     lib.sprot_select_peaks.argtypes = [vp, i32, i32, C.c_float, vp, vp, vp, vp]
@@ -132,7 +134,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
     lib.sprot_kernel_timing_read.restype = None
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
-                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_axis_vote_eps", "sprot_refine_axis",
+                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_axis_vote_eps", "sprot_refine_axis",
                  "sprot_select_peaks",
                  "sprot_estimate_batch",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
@@ -223,6 +225,15 @@ def axis_vote(P, Q, G: int, grid, stream=None):
     _check_points(P, Q)
     st = load().sprot_axis_vote(_ptr(P), _ptr(Q), P.shape[0], int(G), _ptr(grid), _stream(stream))
     check(st, "sprot_axis_vote")
+
+
+def vote_plan(n: int, G: int, batched: bool = False):
+    """The axis vote's work split for n pairs on a G x G grid: dict(band_row0, slices)."""
+    nb, sl = C.c_int32(0), C.c_int32(0)
+    rows = (C.c_int32 * (MAX_BANDS + 1))()
+    check(load().sprot_vote_plan(int(n), int(G), 1 if batched else 0, C.byref(nb), rows, C.byref(sl)),
+          "sprot_vote_plan")
+    return dict(band_row0=list(rows[:nb.value + 1]), slices=sl.value)
 
 
 def axis_vote_sampled(P, Q, G: int, J: int, grid, stream=None):

@@ -330,6 +330,19 @@ int tile_bytes(const InstPlan& ip) {
 
 }  // namespace
 
+bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm) {
+  InstPlan ip{};
+  ip.G = G;
+  *nsm = sm_count(dev);
+  plan_vote(ip, n, true, *nsm);
+  if (ip.T <= 0) return false;
+  *T = ip.T;
+  for (int b = 0; b <= ip.T; ++b) row0[b] = ip.row0[b];
+  *S = ip.S;
+  *tile = tile_bytes(ip);
+  return true;
+}
+
 // Frees the workspace of stream st on the current device (its buffers, graphs, events and
 // second stream), for callers that destroy st; a later stream reusing the handle starts anew.
 void release_workspace(cudaStream_t st) {
@@ -891,6 +904,26 @@ int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t G, uint32
   if (!P || !Q || !grid || n < 1 || !is_pow2(G) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)
     return SPROT_E_INVAL;
   return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream), -1.f);
+}
+
+int sprot_vote_plan(int64_t n, int32_t G, int32_t batched, int32_t* n_bands, int32_t* band_row0,
+                    int32_t* slices) {
+  if (!n_bands || !band_row0 || !slices || n < 1 || n > (int64_t)1 << 31 || !is_pow2(G) ||
+      G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)
+    return SPROT_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SPROT_E_CUDA;
+  }
+  InstPlan ip{};
+  ip.G = G;
+  plan_vote(ip, n, batched == 0, sm_count(dev));
+  if (ip.T <= 0) return SPROT_E_INVAL;
+  *n_bands = ip.T;
+  for (int b = 0; b <= ip.T; ++b) band_row0[b] = ip.row0[b];
+  *slices = ip.S;
+  return SPROT_OK;
 }
 
 int sprot_axis_vote_eps(const float* P, const float* Q, int64_t n, int32_t G, float eps, uint32_t* grid,

@@ -11,7 +11,7 @@
 namespace sprot {
 
 constexpr int kMaxK = SPROT_MAX_K;
-constexpr int kMaxBands = 48;        // row bands of one accumulator (G = 2048 needs 37)
+constexpr int kMaxBands = SPROT_MAX_BANDS;  // row bands of one accumulator (G = 2048 needs 37)
 constexpr int kStreamThreads = 256;  // threads of the per-pair kernels
 constexpr int kStreamChunk = 8192;   // pairs per per-pair work item
 constexpr int kReduceWords = 512;   // accumulator words per slice-reduction item (128 x uint4)
@@ -101,6 +101,10 @@ struct Problem {
 // the results. Returns SPROT_OK, or for a single problem SPROT_E_NOAXIS when it has no peak.
 // graphs: replay the launch sequence from a CUDA graph when its shape repeats (see runtime.cu)
 int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true);
+
+// The axis-vote plan of a single solve of n pairs on a G x G grid on device dev: T row bands
+// (row0[T + 1]), S circle slices, the largest band tile in bytes and the device's SM count.
+bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm);
 
 // Frees the solve() workspace of stream st (call before destroying st).
 void release_workspace(cudaStream_t st);

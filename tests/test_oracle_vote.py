@@ -680,6 +680,21 @@ def test_cell_votes_equal_the_whole_grid():
     assert np.array_equal(lo, av["lo"].ravel()) and np.array_equal(hi, av["hi"].ravel())
 
 
+def test_row_votes_equal_the_whole_grid():
+    """The row-at-a-time evaluator (used on whole rows of the 10^6-pair accumulator) equals
+    the whole-grid accumulator on every row, bounds included, also with chunks smaller than
+    the pair count and degenerate pairs present."""
+    prob = synth.make_problem(300, (0.5,), 0.01, seed=12)
+    P, Q = prob.P.copy(), prob.Q.copy()
+    Q[7] = P[7]  # a degenerate pair
+    G = 32
+    av = oracle.axis_vote(P, Q, G)
+    for row in range(G):
+        cnt, lo, hi = oracle.row_votes(P, Q, G, row, chunk=77)
+        assert np.array_equal(cnt, av["grid"][row])
+        assert np.array_equal(lo, av["lo"][row]) and np.array_equal(hi, av["hi"][row])
+
+
 def test_eps_cell_votes_equal_the_whole_grid():
     P, Q = _mixed_pairs(120, 91)
     G, eps = 32, 0.03
