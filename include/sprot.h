@@ -75,6 +75,7 @@ extern "C" {
 #define SPROT_MAX_ANGLE_BINS 4096
 #define SPROT_MAX_SAMPLES 4096     /* points per circle of the sampled accumulator */
 #define SPROT_MAX_BANDS 48         /* row bands of one accumulator in the axis vote */
+#define SPROT_NOALLOC_SCRATCH_BYTES (40u << 20) /* fixed scratch of sprot_axis_vote_noalloc */
 
 /* Solver parameters. The paper fixes none of them; the defaults are those of
  * sprot_default_params(). */
@@ -170,6 +171,31 @@ int sprot_estimate_rotations_ex(const float* P, const float* Q, int64_t n,
  * overwritten, not accumulated. Errors: E_INVAL (NULL, n < 1, bad G), E_NOMEM, E_CUDA. */
 int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size,
                     uint32_t* grid, void* stream);
+
+/* sprot_axis_vote without any allocation. The paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory -- code running under a host framework that
+ * owns the device heap (its caching allocator, a hard memory cap), a plug-in whose memory is
+ * budgeted by its host process, or a latency-critical path where an allocation may block on
+ * the driver. It computes the same grid as sprot_axis_vote (the same launches and plan) but
+ * takes all its scratch (work tables, queue counter, peak key and the slices' partial
+ * accumulators, S x G x G/2 x 4 bytes for S slices) from one file-scope device array of
+ * SPROT_NOALLOC_SCRATCH_BYTES (40 MB) that every GPU loading the library holds until the
+ * process exits. It calls no cudaMalloc, cudaFree or other allocating routine. The caller
+ * passes P, Q (device, n x 3 float32) and grid (device uint32[G*G], overwritten).
+ * - Limit: a problem whose plan needs more scratch than the array holds is rejected with
+ *   E_INVAL before anything runs. On a 152-SM GPU every n <= 5,177,265 fits for G <= 512,
+ *   n <= 1,245,165 for G = 1024 and n <= 262,140 for G = 2048.
+ * - Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *   capture on the device.
+ * - Sharing: every call on a device uses the same array and leaves the last call's contents
+ *   there; each call clears what must start at zero itself (on the device, in stream order).
+ *   Calls whose work overlaps on the GPU -- on different streams or from different host
+ *   threads without ordering between them -- race on the array and give wrong grids.
+ * Asynchronous on the stream. Errors: E_INVAL (NULL, n < 1, bad G, plan beyond the scratch),
+ * E_CUDA. */
+int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n, int32_t grid_size,
+                            uint32_t* grid, void* stream);
 
 /* The work split of the axis vote (Algorithm 1's accumulator) for n pairs on a G x G grid on
  * the current device, as a single solve (batched = 0) or a batch instance (batched = 1) would

@@ -28,7 +28,7 @@ EXPORTS = [
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
-    "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan",
+    "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan", "sprot_axis_vote_noalloc",
 ]
 
 
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_axis_vote_sampled.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.sprot_axis_vote_eps.argtypes = [vp, vp, i64, i32, C.c_float, vp, vp]
     lib.sprot_vote_plan.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.sprot_axis_vote_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.sprot_refine_axis.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i64), vp]
     lib.sprot_select_peaks.argtypes = [vp, i32, i32, C.c_float, vp, vp, vp, vp]
@@ -134,7 +135,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
     lib.sprot_kernel_timing_read.restype = None
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
-                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_axis_vote_eps", "sprot_refine_axis",
+                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_axis_vote_noalloc", "sprot_axis_vote_eps", "sprot_refine_axis",
                  "sprot_select_peaks",
                  "sprot_estimate_batch",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
