@@ -74,7 +74,7 @@ extern "C" {
 #define SPROT_MAX_GRID 2048
 #define SPROT_MAX_ANGLE_BINS 4096
 #define SPROT_MAX_SAMPLES 4096     /* points per circle of the sampled accumulator */
-#define SPROT_MAX_BANDS 48         /* row bands of one accumulator in the axis vote */
+#define SPROT_MAX_BANDS 96         /* row bands of one accumulator in the axis vote */
 #define SPROT_NOALLOC_SCRATCH_BYTES (40u << 20) /* fixed scratch of sprot_axis_vote_noalloc */
 
 /* Solver parameters. The paper fixes none of them; the defaults are those of

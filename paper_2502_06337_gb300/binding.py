@@ -19,7 +19,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOAXIS, E_UNIMPL, E_BUSY = 0, -1, -2,
 HOST_PTRS = 0x1
 SUBCELL_AXIS = 0x2
 MAX_K = 8
-MAX_BANDS = 48
+MAX_BANDS = 96
 
 EXPORTS = [
     "sprot_default_params", "sprot_status_string", "sprot_estimate_rotation",

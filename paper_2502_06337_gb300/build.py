@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsprot.so")
-SOURCES = ["vote_walk.cu", "vote_sampled.cu", "vote_eps.cu", "post_kernels.cu", "runtime.cu", "server.cu",
+SOURCES = ["vote_runs.cu", "vote_sampled.cu", "vote_eps.cu", "post_kernels.cu", "runtime.cu", "server.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -142,7 +142,7 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   const int threads = 256, blocks = (std::max(n_items, n_ritems) + threads - 1) / threads;
   k_noalloc_setup<<<blocks, threads, 0, st>>>(s);
   launches_add(1);
-  launch_axis_vote_walk(s.items, n_items, s.inst_dev, s.counter, std::min(n_items, nsm), tile, st);
+  launch_axis_vote_runs(s.items, n_items, s.inst_dev, s.counter, std::min(n_items, nsm), tile, st);
   launch_grid_reduce(s.ritems, n_ritems, s.inst_dev, st);
   if (cudaGetLastError() != cudaSuccess) return SPROT_E_CUDA;
   return SPROT_OK;

@@ -125,40 +125,48 @@ int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, i
   return SPROT_OK;
 }
 
-// Row bands of a G x G accumulator. Each band must fit the shared tile (G/2 words per row);
-// band edges split the expected work evenly: random great circles cross the plane with
-// density proportional to 2 / (1 + u^2 + v^2) (the stereographic length element over the
-// uniform density of the sphere), whose integral across a row is
-// (4 / a) atan(1 / a), a = sqrt(1 + v^2).
-void plan_bands(int G, int* n_bands, int32_t* row0) {
-  const int cap = (kMaxSmemBytes - vote_table_bytes()) / (G / 2 * 4);
-  std::vector<double> cum(G + 1, 0.0);
+// Row bands of a G x G accumulator. Each band must fit the shared tiles (row_bytes per row
+// beside table_bytes of per-warp tables, smem_bytes in all); band edges are even rows (the curve vote's row tile
+// packs two rows per word) and split the expected work evenly: random great circles cross the
+// plane with density proportional to 2 / (1 + u^2 + v^2) (the stereographic length element over
+// the uniform density of the sphere), whose integral across a row is (4 / a) atan(1 / a),
+// a = sqrt(1 + v^2).
+void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_bands, int32_t* row0) {
+  const int cap = ((smem_bytes - table_bytes) / row_bytes) & ~1;  // rows per band, even
+  const int P = G / 2, capp = cap / 2;                                 // row pairs
+  std::vector<double> cum(P + 1, 0.0);
   for (int r = 0; r < G; ++r) {
     double v = -1.0 + (2.0 * r + 1.0) / G, a = std::sqrt(1.0 + v * v);
-    cum[r + 1] = cum[r] + 4.0 / a * std::atan(1.0 / a);
+    cum[r / 2 + 1] += 4.0 / a * std::atan(1.0 / a);
   }
-  for (int T = (G + cap - 1) / cap; T <= kMaxBands; ++T) {
+  for (int q = 0; q < P; ++q) cum[q + 1] += cum[q];
+  for (int T = (P + capp - 1) / capp; T <= kMaxBands; ++T) {
     std::vector<int32_t> e(T + 1);
     e[0] = 0;
-    e[T] = G;
+    e[T] = P;
     for (int b = 1; b < T; ++b) {
-      double target = cum[G] * b / T;
+      double target = cum[P] * b / T;
       int r = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
-      int lo = std::max(e[b - 1] + 1, G - (T - b) * cap);  // the rest must still fit
-      int hi = std::min(e[b - 1] + cap, G - (T - b));
+      int lo = std::max(e[b - 1] + 1, P - (T - b) * capp);  // the rest must still fit
+      int hi = std::min(e[b - 1] + capp, P - (T - b));
       e[b] = std::min(std::max(r, lo), hi);
     }
     bool fits = true;
-    for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= cap && e[b + 1] > e[b];
+    for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= capp && e[b + 1] > e[b];
     if (fits) {
       *n_bands = T;
-      for (int b = 0; b <= T; ++b) row0[b] = e[b];
+      for (int b = 0; b <= T; ++b) row0[b] = 2 * e[b];
       return;
     }
   }
-  // unreachable for G <= 2048 (cap >= 56 rows)
+  // unreachable for G <= 2048 (cap >= 22 rows)
   *n_bands = 0;
 }
+
+// Shared bytes per accumulator row: the curve vote keeps a row-difference and a
+// column-difference tile (G/2 words each per row), the eps-band vote one tile of G/2 words.
+inline int vote_row_bytes(int G) { return 4 * G; }
+inline int eps_row_bytes(int G) { return 2 * G; }
 
 struct InstPlan {
   int64_t n;
@@ -314,18 +322,21 @@ int batch_chunk(int64_t total) {
 // Vote layout of one instance: row bands that fit the shared tile, and circle slices (at most
 // 65535 circles each, so the 16-bit counters cannot overflow). A single problem is spread
 // over every SM; in a batch each instance gets slices of 32768 circles.
-void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm) {
-  plan_bands(ip.G, &ip.T, ip.row0);
+void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false) {
+  if (eps)
+    plan_bands(ip.G, kMaxSmemBytes, eps_row_bytes(ip.G), 0, &ip.T, ip.row0);
+  else
+    plan_bands(ip.G, kRunSmemBytes, vote_row_bytes(ip.G), vote_run_table_bytes(), &ip.T, ip.row0);
   const int64_t s_min = (n + kMaxSliceCircles - 1) / kMaxSliceCircles;
   int64_t s = single ? std::max<int64_t>(1, nsm / std::max(ip.T, 1)) : (n + 32767) / 32768;
   s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
   ip.S = (int)std::max(s, s_min);
 }
 
-int tile_bytes(const InstPlan& ip) {
+int tile_bytes(const InstPlan& ip, bool eps = false) {
   int rows = 0;
   for (int b = 0; b < ip.T; ++b) rows = std::max(rows, ip.row0[b + 1] - ip.row0[b]);
-  return rows * (ip.G / 2) * 4;
+  return rows * (eps ? eps_row_bytes(ip.G) : vote_row_bytes(ip.G));
 }
 
 }  // namespace
@@ -361,9 +372,6 @@ void release_workspace(cudaStream_t st) {
 }
 
 size_t problem_footprint(int64_t n, int G, int J, int k) {
-  int T = 0;
-  int32_t row0[kMaxBands + 1];
-  plan_bands(G, &T, row0);
   int64_t S = std::max<int64_t>((n + 32767) / 32768, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
   int64_t items = (n + stream_chunk(n) - 1) / stream_chunk(n);
   return align_up((size_t)S * G * (G / 2) * 4) + align_up((size_t)G * G * 4) +
@@ -629,7 +637,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
       vt.emplace(st);
     else
       ok &= ck(cudaEventRecord(ws->tv0, st));
-    launch_axis_vote_walk(dvit, (int)vitems.size(), dinst, dcounter,
+    launch_axis_vote_runs(dvit, (int)vitems.size(), dinst, dcounter,
                           std::min((int)vitems.size(), nsm), vote_tile, st);
     if (direct)
       vt->stop(st);
@@ -732,9 +740,9 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   const int nsm = sm_count(ws->device);
   InstPlan ip{};
   ip.G = G;
-  plan_vote(ip, n, true, nsm);
+  plan_vote(ip, n, true, nsm, eps >= 0.f);
   if (ip.T <= 0) return SPROT_E_INVAL;
-  const int smem = tile_bytes(ip);
+  const int smem = tile_bytes(ip, eps >= 0.f);
   std::vector<VoteItem> vit;
   for (int sl = 0; sl < ip.S; ++sl)
     for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
@@ -778,7 +786,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   const int nit = (int)vit.size();
   if (eps < 0.f) {
     VoteTimer vt(st);
-    launch_axis_vote_walk(dv, nit, di, dc, std::min(nit, nsm), smem, st);
+    launch_axis_vote_runs(dv, nit, di, dc, std::min(nit, nsm), smem, st);
     vt.stop(st);
   } else {
     launch_axis_vote_eps(dv, nit, di, dc, std::min(nit, nsm), smem, eps, st);

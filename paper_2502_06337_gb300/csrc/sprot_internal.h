@@ -11,11 +11,12 @@
 namespace sprot {
 
 constexpr int kMaxK = SPROT_MAX_K;
-constexpr int kMaxBands = SPROT_MAX_BANDS;  // row bands of one accumulator (G = 2048 needs 37)
+constexpr int kMaxBands = SPROT_MAX_BANDS;  // row bands of one accumulator (G = 2048 needs 94)
 constexpr int kStreamThreads = 256;  // threads of the per-pair kernels
 constexpr int kStreamChunk = 8192;   // pairs per per-pair work item
 constexpr int kReduceWords = 512;   // accumulator words per slice-reduction item (128 x uint4)
 constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // tile; leaves room for static shared
+constexpr int kRunSmemBytes = 227 * 1024 - 64;    // the curve vote's tiles and tables (16 B static)
 constexpr int kMaxSliceCircles = 65535;  // u16 tile counters: at most this many circles/slice
 
 // Device-side result of one rotation; mirrors sprot_rotation plus internals.
@@ -113,10 +114,12 @@ void release_workspace(cudaStream_t st);
 size_t problem_footprint(int64_t n, int G, int J, int k);
 
 // ---- launchers -------------------------------------------------------------------------
-// Axis vote (vote_walk.cu). tile_bytes: the largest band tile of the launch; the kernel adds
-// its per-warp circle tables and per-lane dummy vote words (vote_table_bytes()) to the dynamic
-// shared memory.
-int vote_table_bytes();
+// Axis vote (vote_runs.cu). tile_bytes: the largest band's two tiles (4 G bytes per row); the
+// kernel adds its per-warp circle tables and per-lane dummy vote words (vote_run_table_bytes())
+// to the dynamic shared memory.
+int vote_run_table_bytes();
+void launch_axis_vote_runs(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
+                           int grid_ctas, int tile_bytes, cudaStream_t st);
 // eps-band accumulator of Eq. 9 (vote_eps.cu): same items, tiles and partials as the curve vote.
 void launch_axis_vote_eps(const VoteItem* items, int n_items, const InstDev* insts, int* counter, int grid_ctas,
                           int tile_bytes, float eps, cudaStream_t st);
@@ -129,8 +132,6 @@ void launch_axis_ls(const float* P, const float* Q, int64_t n, const int32_t* la
 // point of every circle, J points per circle.
 int launch_axis_vote_sampled(const float* P, const float* Q, int64_t n, int G, int J, uint32_t* grid,
                              int n_sm, cudaStream_t st);
-void launch_axis_vote_walk(const VoteItem* items, int n_items, const InstDev* insts, int* counter,
-                           int grid_ctas, int tile_bytes, cudaStream_t st);
 // The slice reduction, suppression rounds, angle vote and FP64 sums finish each instance in the
 // last block to arrive (peaks, angle peak and Rodrigues, Kabsch) when InstDev::done is set.
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
