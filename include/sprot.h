@@ -178,13 +178,13 @@ int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t grid_size
  * budgeted by its host process, or a latency-critical path where an allocation may block on
  * the driver. It computes the same grid as sprot_axis_vote (the same launches and plan) but
  * takes all its scratch (work tables, queue counter, peak key and the slices' partial
- * accumulators, S x G x G/2 x 4 bytes for S slices) from one file-scope device array of
+ * accumulators, 2 x S x G x G/2 x 4 bytes for S slices) from one file-scope device array of
  * SPROT_NOALLOC_SCRATCH_BYTES (40 MB) that every GPU loading the library holds until the
  * process exits. It calls no cudaMalloc, cudaFree or other allocating routine. The caller
  * passes P, Q (device, n x 3 float32) and grid (device uint32[G*G], overwritten).
  * - Limit: a problem whose plan needs more scratch than the array holds is rejected with
- *   E_INVAL before anything runs. On a 152-SM GPU every n <= 5,177,265 fits for G <= 512,
- *   n <= 1,245,165 for G = 1024 and n <= 262,140 for G = 2048.
+ *   E_INVAL before anything runs. On a 152-SM GPU every n <= 2,555,865 fits for G <= 512,
+ *   n <= 589,815 for G = 1024 and n <= 131,070 for G = 2048.
  * - Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before any stream
  *   capture on the device.
@@ -199,10 +199,11 @@ int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n, int32_t g
 
 /* The work split of the axis vote (Algorithm 1's accumulator) for n pairs on a G x G grid on
  * the current device, as a single solve (batched = 0) or a batch instance (batched = 1) would
- * use it: the accumulator is cut into *n_bands row bands, band b covering rows
- * [band_row0[b], band_row0[b+1]) (band_row0: host int32[SPROT_MAX_BANDS + 1]), and the pairs
- * into *slices consecutive slices of at most 65535 circles. Host-only; for tests and tuning.
- * Errors: E_INVAL (NULL, n < 1, bad G), E_CUDA (no device). */
+ * use it: the pairs are cut into *slices consecutive slices of at most 65535 circles, and each
+ * slice is voted band by band: *n_bands bands, band b covering rows (for the curve's caps that
+ * are walked along rows) and columns (for those walked along columns) [band_row0[b],
+ * band_row0[b+1]) (band_row0: host int32[SPROT_MAX_BANDS + 1]). Host-only; for tests and
+ * tuning. Errors: E_INVAL (NULL, n < 1, bad G), E_CUDA (no device). */
 int sprot_vote_plan(int64_t n, int32_t grid_size, int32_t batched, int32_t* n_bands,
                     int32_t* band_row0, int32_t* slices);
 

@@ -53,8 +53,9 @@ __global__ void k_noalloc_setup(const NoallocSetup s) {
     *s.peak = 0ull;
   }
   if (t < s.n_items) {
-    const int sl = t / s.T, b = t - sl * s.T;
-    s.items[t] = VoteItem{0, b, sl, 0, s.n * sl / s.S, s.n * (sl + 1) / s.S};
+    // slice sl, band b, kind kd (0: the row caps -> partial sl, 1: the column caps -> S + sl)
+    const int sl = t / (2 * s.T), r = t - sl * 2 * s.T, b = r >> 1, kd = r & 1;
+    s.items[t] = VoteItem{0, b, kd * s.S + sl, kd, s.n * sl / s.S, s.n * (sl + 1) / s.S};
   }
   if (t < s.n_ritems) {
     const int64_t w0 = (int64_t)t * kReduceWords;
@@ -82,7 +83,7 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   int T = 0, S = 0, tile = 0, nsm = 0;
   NoallocSetup s{};
   if (!single_vote_plan(n, G, dev, &T, s.inst.band_row0, &S, &tile, &nsm)) return SPROT_E_INVAL;
-  const int n_items = T * S;
+  const int n_items = 2 * T * S;
   const int64_t words = (int64_t)G * (G / 2);
   const int n_ritems = (int)((words + kReduceWords - 1) / kReduceWords);
   // layout of the scratch
@@ -98,7 +99,7 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   const size_t o_peak = off;
   off = align_na(off + sizeof(unsigned long long));
   const size_t o_partial = off;
-  off = align_na(off + (size_t)S * words * 4);
+  off = align_na(off + (size_t)2 * S * words * 4);
   if (off > (size_t)SPROT_NOALLOC_SCRATCH_BYTES) return SPROT_E_INVAL;  // beyond the fixed scratch
   // the scratch's device address on this device (looked up once per device)
   char* base = nullptr;
@@ -123,7 +124,7 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   d.G = G;
   d.k = 1;
   d.n_bands = T;
-  d.S = S;
+  d.S = 2 * S;  // partials: the row caps' and the column caps' of every slice
   d.partial = reinterpret_cast<uint32_t*>(base + o_partial);
   d.grid = grid;
   d.peak_key = reinterpret_cast<unsigned long long*>(base + o_peak);

@@ -125,19 +125,21 @@ int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, i
   return SPROT_OK;
 }
 
-// Row bands of a G x G accumulator. Each band must fit the shared tiles (row_bytes per row
-// beside table_bytes of per-warp tables, smem_bytes in all); band edges are even rows (the curve vote's row tile
-// packs two rows per word) and split the expected work evenly: random great circles cross the
-// plane with density proportional to 2 / (1 + u^2 + v^2) (the stereographic length element over
-// the uniform density of the sphere), whose integral across a row is (4 / a) atan(1 / a),
-// a = sqrt(1 + v^2).
+// Bands of a G x G accumulator (of rows; the curve vote cuts its columns at the same edges).
+// Each band must fit the shared tile (row_bytes per row beside table_bytes of per-warp tables,
+// smem_bytes in all); band edges are multiples of 8 (the curve vote's tiles pack two rows or
+// two columns per word and write them with 16-byte stores) and split the expected work evenly:
+// random great circles cross the plane with density proportional to 2 / (1 + u^2 + v^2) (the
+// stereographic length element over the uniform density of the sphere), whose integral across a
+// row is (4 / a) atan(1 / a), a = sqrt(1 + v^2).
 void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_bands, int32_t* row0) {
-  const int cap = ((smem_bytes - table_bytes) / row_bytes) & ~1;  // rows per band, even
-  const int P = G / 2, capp = cap / 2;                                 // row pairs
+  constexpr int U = 8;  // rows per planning unit
+  const int cap = (smem_bytes - table_bytes) / row_bytes;
+  const int P = G / U, capp = cap / U;  // units in all, per band
   std::vector<double> cum(P + 1, 0.0);
   for (int r = 0; r < G; ++r) {
     double v = -1.0 + (2.0 * r + 1.0) / G, a = std::sqrt(1.0 + v * v);
-    cum[r / 2 + 1] += 4.0 / a * std::atan(1.0 / a);
+    cum[r / U + 1] += 4.0 / a * std::atan(1.0 / a);
   }
   for (int q = 0; q < P; ++q) cum[q + 1] += cum[q];
   for (int T = (P + capp - 1) / capp; T <= kMaxBands; ++T) {
@@ -155,17 +157,18 @@ void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_ba
     for (int b = 0; b < T; ++b) fits &= (e[b + 1] - e[b]) <= capp && e[b + 1] > e[b];
     if (fits) {
       *n_bands = T;
-      for (int b = 0; b <= T; ++b) row0[b] = 2 * e[b];
+      for (int b = 0; b <= T; ++b) row0[b] = U * e[b];
       return;
     }
   }
-  // unreachable for G <= 2048 (cap >= 22 rows)
+  // unreachable for G <= 2048 (cap >= 88 rows)
   *n_bands = 0;
 }
 
-// Shared bytes per accumulator row: the curve vote keeps a row-difference and a
-// column-difference tile (G/2 words each per row), the eps-band vote one tile of G/2 words.
-inline int vote_row_bytes(int G) { return 4 * G; }
+// Shared bytes per accumulator row (or column) of a band: the curve vote's tile holds G/2 words
+// per row of a row band (two rows share a word) and per column of a column band; the eps-band
+// vote's tile G/2 words per row.
+inline int vote_row_bytes(int G) { return 2 * G; }
 inline int eps_row_bytes(int G) { return 2 * G; }
 
 struct InstPlan {
@@ -328,7 +331,9 @@ void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false) 
   else
     plan_bands(ip.G, kRunSmemBytes, vote_row_bytes(ip.G), vote_run_table_bytes(), &ip.T, ip.row0);
   const int64_t s_min = (n + kMaxSliceCircles - 1) / kMaxSliceCircles;
-  int64_t s = single ? std::max<int64_t>(1, nsm / std::max(ip.T, 1)) : (n + 32767) / 32768;
+  // the curve vote has 2 T items per slice (row bands and column bands), the eps-band vote T
+  const int per_slice = (eps ? 1 : 2) * std::max(ip.T, 1);
+  int64_t s = single ? std::max<int64_t>(1, nsm / per_slice) : (n + 32767) / 32768;
   s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
   ip.S = (int)std::max(s, s_min);
 }
@@ -374,7 +379,7 @@ void release_workspace(cudaStream_t st) {
 size_t problem_footprint(int64_t n, int G, int J, int k) {
   int64_t S = std::max<int64_t>((n + 32767) / 32768, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
   int64_t items = (n + stream_chunk(n) - 1) / stream_chunk(n);
-  return align_up((size_t)S * G * (G / 2) * 4) + align_up((size_t)G * G * 4) +
+  return align_up((size_t)2 * S * G * (G / 2) * 4) + align_up((size_t)G * G * 4) +
          align_up((size_t)k * n * 2) + align_up((size_t)2 * items * k * 80) + align_up((size_t)n * 4) +
          align_up((size_t)k * J * 4) + align_up(sizeof(DevRot) * k) + 4096;
 }
@@ -461,7 +466,10 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     vote_tile = std::max(vote_tile, tile_bytes(ip));
     for (int sl = 0; sl < ip.S; ++sl) {
       int64_t c0 = pb.n * sl / ip.S, c1 = pb.n * (sl + 1) / ip.S;
-      for (int b = 0; b < ip.T; ++b) vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});
+      for (int b = 0; b < ip.T; ++b) {
+        vitems.push_back(VoteItem{i, b, sl, 0, c0, c1});         // row caps -> partial sl
+        vitems.push_back(VoteItem{i, b, ip.S + sl, 1, c0, c1});  // column caps -> partial S + sl
+      }
     }
     int64_t words = (int64_t)ip.G * (ip.G / 2);
     const int64_t red_words =
@@ -516,7 +524,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   for (int i = 0; i < m; ++i) {
     InstPlan& ip = plan[i];
     const Problem& pb = probs[i];
-    ip.o_partial = take((size_t)ip.S * ip.G * (ip.G / 2) * 4);
+    ip.o_partial = take((size_t)2 * ip.S * ip.G * (ip.G / 2) * 4);
     ip.o_grid = take((size_t)ip.G * ip.G * 4);
     ip.o_bins = take((size_t)ip.k * ip.n * 2);
     ip.o_msum = take((size_t)2 * ip.n_items * ip.k * 10 * 8);
@@ -571,7 +579,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     d.w = ip.w;
     d.window = ip.window;
     d.n_bands = ip.T;
-    d.S = ip.S;
+    d.S = 2 * ip.S;  // partials: the row caps' and the column caps' of every slice
     d.subcell = (pb.prm.flags & SPROT_SUBCELL_AXIS) ? 1 : 0;
     d.tau = ip.tau;
     d.cos_nms = ip.cos_nms;
@@ -728,7 +736,6 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   return m == 1 ? worst : SPROT_OK;
 }
 
-// Accumulator only (stage entry point): vote + slice reduction into a caller grid.
 // Accumulator only (stage entry points): the curve vote (eps < 0) or the eps-band vote of
 // Eq. 9 (eps >= 0), then the slice reduction into a caller grid.
 int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* grid,
@@ -743,9 +750,13 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   plan_vote(ip, n, true, nsm, eps >= 0.f);
   if (ip.T <= 0) return SPROT_E_INVAL;
   const int smem = tile_bytes(ip, eps >= 0.f);
+  // the curve vote votes every slice twice (row bands: partial sl; column bands: partial S + sl)
+  const int kinds = eps >= 0.f ? 1 : 2;
   std::vector<VoteItem> vit;
   for (int sl = 0; sl < ip.S; ++sl)
-    for (int b = 0; b < ip.T; ++b) vit.push_back(VoteItem{0, b, sl, 0, n * sl / ip.S, n * (sl + 1) / ip.S});
+    for (int b = 0; b < ip.T; ++b)
+      for (int kd = 0; kd < kinds; ++kd)
+        vit.push_back(VoteItem{0, b, kd * ip.S + sl, kd, n * sl / ip.S, n * (sl + 1) / ip.S});
   std::vector<ReduceItem> rit;
   int64_t words = (int64_t)G * (G / 2);
   for (int64_t w0 = 0; w0 < words; w0 += kReduceWords) rit.push_back(ReduceItem{0, 0, w0, std::min<int64_t>(w0 + kReduceWords, words)});
@@ -756,7 +767,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   size_t hdr = off;
   size_t o_zero = take(sizeof(int)), o_peak = take(8);
   size_t zend = off;
-  size_t o_part = take((size_t)ip.S * G * (G / 2) * 4);
+  size_t o_part = take((size_t)kinds * ip.S * G * (G / 2) * 4);
   status = ws->reserve(off, hdr);
   if (status != SPROT_OK) return status;
   char* D = ws->dev;
@@ -771,7 +782,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   d.G = G;
   d.k = 1;
   d.n_bands = ip.T;
-  d.S = ip.S;
+  d.S = kinds * ip.S;
   for (int b = 0; b <= ip.T; ++b) d.band_row0[b] = ip.row0[b];
   d.partial = reinterpret_cast<uint32_t*>(D + o_part);
   d.grid = grid;
@@ -784,10 +795,11 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   const InstDev* di = reinterpret_cast<InstDev*>(D + o_inst);
   int* dc = reinterpret_cast<int*>(D + o_zero);
   const int nit = (int)vit.size();
+  std::optional<VoteTimer> vt;
   if (eps < 0.f) {
-    VoteTimer vt(st);
+    vt.emplace(st);
     launch_axis_vote_runs(dv, nit, di, dc, std::min(nit, nsm), smem, st);
-    vt.stop(st);
+    vt->stop(st);
   } else {
     launch_axis_vote_eps(dv, nit, di, dc, std::min(nit, nsm), smem, eps, st);
   }

@@ -43,7 +43,8 @@ struct InstDev {
   const float* Qv;
   int64_t n;
   int32_t G, J, k, w, window;
-  int32_t n_bands, S;            // row bands and circle slices of the axis vote
+  int32_t n_bands, S;            // bands and partial slices of the axis vote (the curve vote
+                                 // writes two partials per slice of circles: rows, columns)
   int32_t subcell;               // axis at the sub-cell peak (SPROT_SUBCELL_AXIS)
   float tau;
   double cos_nms;                // cosine of the suppression radius between axis lines
@@ -69,7 +70,9 @@ struct InstDev {
 };
 
 struct VoteItem {
-  int32_t inst, band, slice, pad;
+  int32_t inst, band, slice;
+  int32_t kind;    // curve vote: 0 the row caps of band `band` of rows, 1 the column caps of band
+                   // `band` of columns (the same band edges); the eps-band vote: 0
   int64_t c0, c1;  // circle range [c0, c1)
 };
 

@@ -53,10 +53,10 @@ namespace sprot {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRunThreads = 512;  // 16 warps
+constexpr int kRunThreads = 768;  // 24 warps
 constexpr int kRunWarps = kRunThreads / 32;
-constexpr int kSeg = 16;          // units per segment of phase B
-constexpr int kWalkers = 2;       // independent walkers per lane (instruction-level parallelism)
+constexpr int kSeg = 12;          // units per segment of phase B
+constexpr int kWalkers = 1;       // walkers per lane (more lengthen each deal's longest segment)
 
 // Per-warp circle table in shared memory, one column per lane (structure of arrays): 0 d1, 1 d2,
 // 2 d3, 3-6 the unit ranges of the caps (lo | hi << 16: 0 top rows, walked up; 1 bottom rows,
@@ -65,10 +65,15 @@ constexpr int kWalkers = 2;       // independent walkers per lane (instruction-l
 constexpr int kRec = 9;
 constexpr int kTab = kRec * 32;
 
+// The work item's part of the grid: rows [R0, R1) x columns [C0, C1) (a band of rows for the
+// row caps, a band of columns for the column caps) and its shared tile at byte address tb: for
+// rows, (R1 - R0)/2 x G words (word (i, j) holds rows R0 + 2i and R0 + 2i + 1 of column j); for
+// columns, G x W words with W = (C1 - C0)/2 (word (i, j) holds columns C0 + 2j and C0 + 2j + 1
+// of row i).
 struct Band {
-  int G, R0, R1;
+  int G, R0, R1, C0, C1, W;
   float step, half;
-  uint32_t rt, ct;  // shared byte addresses of the row-difference and column-difference tiles
+  uint32_t tb;
 };
 
 __device__ __forceinline__ uint32_t range16(int lo, int hi) {  // [lo, hi) or empty
@@ -120,10 +125,43 @@ __device__ __forceinline__ bool wrange(float R2, float dmin, float dmax, float& 
   return true;
 }
 
-// Phase A (one lane, one circle): the caps of its curve in this band, culled to where the curve
-// crosses the band (columns) and the grid (rows), with a margin of mg cells for the float32
-// error of the bounds. Exact horizontal and vertical lines (through the origin, hence along the
-// grid's middle lattice lines) are voted here directly.
+// Geometry shared by the two orientations (so that they agree on which one votes each cell): a
+// circle whose centre lies near the grid has its centre cell (ic, jc) and the 45-degree split
+// M = floor(R / sqrt 2) in cells (rows |i - ic| >= M belong to the row caps); any other curve is
+// voted by rows when |d2| >= |d1| and by columns otherwise.
+struct Geo {
+  float nd, invC, cu, cv, R;
+  int ic, jc, M;
+  bool nearc;
+};
+
+__device__ __forceinline__ Geo geo_of(float d1, float d2, float d3, float half) {
+  Geo g;
+  g.nd = sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
+  g.invC = d3 > 0.f ? __frcp_rn(d3) : __int_as_float(0x7f800000);
+  g.cu = g.cv = g.R = 0.f;
+  g.ic = g.jc = g.M = 0;
+  g.nearc = false;
+  if (d3 > 0.f) {
+    g.cu = -d1 * g.invC;
+    g.cv = -d2 * g.invC;
+    g.nearc = fabsf(g.cu) <= 4.f && fabsf(g.cv) <= 4.f;
+  }
+  if (g.nearc) {
+    g.R = g.nd * g.invC;
+    g.ic = cellf(g.cv, half);
+    g.jc = cellf(g.cu, half);
+    g.M = max(1, __float2int_rd(g.R * half * 0.70710678f));
+  }
+  return g;
+}
+
+// Phase A (one lane, one circle): the caps of its curve that this item votes (ROWS: the top and
+// bottom caps within the item's rows; else the left and right caps within its columns), culled
+// to where the curve crosses the item's part of the grid, with a margin of mg cells for the
+// float32 error of the bounds. Exact horizontal and vertical lines (through the origin, hence
+// along the grid's middle lattice lines) are voted here directly.
+template <bool ROWS>
 __device__ __forceinline__ void prepare(const Band& B, float d1, float d2, float d3, Prepared& S) {
   const int G = B.G;
   const float half = B.half, step = B.step;
@@ -131,76 +169,76 @@ __device__ __forceinline__ void prepare(const Band& B, float d1, float d2, float
 #pragma unroll
   for (int c = 0; c < 4; ++c) S.cap[c] = 0u;
   S.clip = 0u;
-  const float nd = sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
-  if (d3 <= 1e-8f * nd) d3 = 0.f;  // a line through the origin (F changes by under 2e-8 |d|)
+  {
+    const float nd = sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
+    if (d3 <= 1e-8f * nd) d3 = 0.f;  // a line through the origin (F changes by under 2e-8 |d|)
+  }
   S.d1 = d1;
   S.d2 = d2;
   S.d3 = d3;
   if (d3 == 0.f && (d1 == 0.f || d2 == 0.f)) {
-    if (d1 == 0.f) {  // F = 2 d2 v: the rows on both sides of v = 0, whole
+    if (ROWS && d1 == 0.f) {  // F = 2 d2 v: the rows on both sides of v = 0, whole
       for (int r = G / 2 - 1; r <= G / 2; ++r)
         if (r >= B.R0 && r < B.R1)
-          red_add(B.rt + 4u * (uint32_t)(((r - B.R0) >> 1) * G), ((r - B.R0) & 1) ? 0x10000u : 1u);
-    } else {  // F = 2 d1 u: the columns on both sides of u = 0, over the band's rows
-      for (int c = G / 2 - 1; c <= G / 2; ++c) red_add(B.ct + 4u * (uint32_t)(c >> 1), (c & 1) ? 0x10000u : 1u);
+          red_add(B.tb + 4u * (uint32_t)(((r - B.R0) >> 1) * G), ((r - B.R0) & 1) ? 0x10000u : 1u);
+    }
+    if (!ROWS && d2 == 0.f) {  // F = 2 d1 u: the columns on both sides of u = 0, whole
+      for (int c = G / 2 - 1; c <= G / 2; ++c)
+        if (c >= B.C0 && c < B.C1) red_add(B.tb + 4u * (uint32_t)((c - B.C0) >> 1), (c & 1) ? 0x10000u : 1u);
     }
     return;
   }
-  const float V0 = fmaf((float)B.R0, step, -1.f), V1 = fmaf((float)B.R1, step, -1.f);
-  const float invC = d3 > 0.f ? __frcp_rn(d3) : __int_as_float(0x7f800000);
-  float cu = 0.f, cv = 0.f;
-  bool nearc = false;
-  if (d3 > 0.f) {
-    cu = -d1 * invC;
-    cv = -d2 * invC;
-    nearc = fabsf(cu) <= 4.f && fabsf(cv) <= 4.f;
-  }
-  if (nearc) {
-    const float R = nd * invC, R2 = R * R;
-    const int ic = cellf(cv, half), jc = cellf(cu, half);
-    const int M = max(1, __float2int_rd(R * half * 0.70710678f));
+  const Geo g = geo_of(d1, d2, d3, half);
+  if (g.nearc) {
+    const float R2 = g.R * g.R, cu = g.cu, cv = g.cv;
     float lo, hi;
-    // rows: the top and bottom arcs within the grid's columns u in [-1, 1]
-    if (wrange(R2, fmaxf(fmaxf(-1.f - cu, cu - 1.f), 0.f), fmaxf(fabsf(-1.f - cu), fabsf(1.f - cu)), lo, hi)) {
-      const int t0 = max(max(cellf(cv + lo, half) - mg, ic + M), B.R0);
-      const int t1 = min(cellf(cv + hi, half) + mg, B.R1 - 1);
-      const int b0 = max(cellf(cv - hi, half) - mg, B.R0);
-      const int b1 = min(min(cellf(cv - lo, half) + mg, ic - M), B.R1 - 1);
-      S.cap[0] = range16(t0, t1 + 1);
-      S.cap[1] = range16(b0, b1 + 1);
-    }
-    // columns: the left and right arcs within the rows they vote
-    const int clo = max(B.R0, ic - M + 1), chi = min(B.R1 - 1, ic + M - 1);
-    if (clo <= chi) {
-      S.clip = (uint32_t)clo | ((uint32_t)chi << 16);
-      const float Va = fmaf((float)clo, step, -1.f), Vb = fmaf((float)(chi + 1), step, -1.f);
-      if (wrange(R2, fmaxf(fmaxf(Va - cv, cv - Vb), 0.f), fmaxf(fabsf(Va - cv), fabsf(Vb - cv)), lo, hi)) {
-        S.cap[2] = range16(max(cellf(cu - hi, half) - mg, 0), min(cellf(cu - lo, half) + mg, G - 1) + 1);
-        S.cap[3] = range16(max(cellf(cu + lo, half) - mg, 0), min(cellf(cu + hi, half) + mg, G - 1) + 1);
+    if (ROWS) {
+      // the top and bottom arcs within the grid's columns u in [-1, 1]
+      if (wrange(R2, fmaxf(fmaxf(-1.f - cu, cu - 1.f), 0.f), fmaxf(fabsf(-1.f - cu), fabsf(1.f - cu)), lo, hi)) {
+        const int t0 = max(max(cellf(cv + lo, half) - mg, g.ic + g.M), B.R0);
+        const int t1 = min(cellf(cv + hi, half) + mg, B.R1 - 1);
+        const int b0 = max(cellf(cv - hi, half) - mg, B.R0);
+        const int b1 = min(min(cellf(cv - lo, half) + mg, g.ic - g.M), B.R1 - 1);
+        S.cap[0] = range16(t0, t1 + 1);
+        S.cap[1] = range16(b0, b1 + 1);
+      }
+    } else {
+      // the left and right arcs within the rows they vote and the item's columns
+      const int clo = max(0, g.ic - g.M + 1), chi = min(G - 1, g.ic + g.M - 1);
+      if (clo <= chi) {
+        S.clip = (uint32_t)clo | ((uint32_t)chi << 16);
+        const float Va = fmaf((float)clo, step, -1.f), Vb = fmaf((float)(chi + 1), step, -1.f);
+        if (wrange(R2, fmaxf(fmaxf(Va - cv, cv - Vb), 0.f), fmaxf(fabsf(Va - cv), fabsf(Vb - cv)), lo, hi)) {
+          S.cap[2] = range16(max(cellf(cu - hi, half) - mg, B.C0), min(cellf(cu - lo, half) + mg, B.C1 - 1) + 1);
+          S.cap[3] = range16(max(cellf(cu + lo, half) - mg, B.C0), min(cellf(cu + hi, half) + mg, B.C1 - 1) + 1);
+        }
       }
     }
     return;
   }
   // A far circle or a line: nearly straight over the grid, voted in one orientation and walked
   // toward its extreme (the near arc of a circle whose centre lies below the grid is walked up).
-  // The walked range is the arc's extent between the two bounding lines of the other axis (the
-  // grid's columns for rows, the band's rows for columns), from its crossings with them and its
-  // extreme point when that lies between them; without both crossings it is not culled.
+  // The walked range is the arc's extent between the grid's two bounding lines of the other
+  // axis, from its crossings with them and its extreme point when that lies between them;
+  // without both crossings it is not culled.
   const bool rows = fabsf(d2) >= fabsf(d1);
-  const float a = rows ? d1 : d2;   // coefficient of the run axis
-  const float bw = rows ? d2 : d1;  // coefficient of the walked axis
-  const float L0 = rows ? -1.f : V0, L1 = rows ? 1.f : V1;
+  if (rows != ROWS) return;
+  const float a = ROWS ? d1 : d2;   // coefficient of the run axis
+  const float bw = ROWS ? d2 : d1;  // coefficient of the walked axis
+  // crossings with the bounding lines x = -1 and x = 1 of the run axis: roots in the walked axis
+  // of C y^2 + 2 bw y - T(x), T(x) = C - x (C x + 2 a)
+  const float L0 = -1.f, L1 = 1.f;
   float e0, e1;
-  const bool k0 = near_root(d3, invC, bw, fmaf(-L0, fmaf(d3, L0, 2.f * a), d3), e0);
-  const bool k1 = near_root(d3, invC, bw, fmaf(-L1, fmaf(d3, L1, 2.f * a), d3), e1);
-  const int lim0 = rows ? B.R0 : 0, lim1 = rows ? B.R1 - 1 : G - 1;
+  const bool k0 = near_root(d3, g.invC, bw, fmaf(-L0, fmaf(d3, L0, 2.f * a), d3), e0);
+  const bool k1 = near_root(d3, g.invC, bw, fmaf(-L1, fmaf(d3, L1, 2.f * a), d3), e1);
+  const int lim0 = ROWS ? B.R0 : B.C0, lim1 = ROWS ? B.R1 - 1 : B.C1 - 1;
   int w0 = lim0, w1 = lim1;
   if (k0 && k1) {
     float lo = fminf(e0, e1), hi = fmaxf(e0, e1);
-    const float ca = -a * invC;  // the extreme point's run coordinate (inf for a line)
+    const float ca = -a * g.invC;  // the extreme point's run coordinate (inf for a line)
     if (d3 > 0.f && ca >= L0 && ca <= L1) {
       // the extreme's walked coordinate on the near arc, cancellation-free
-      const float ext = copysignf(fmaf(a, a, d3 * d3) / (d3 * (nd + fabsf(bw))), bw);
+      const float ext = copysignf(fmaf(a, a, d3 * d3) / (d3 * (g.nd + fabsf(bw))), bw);
       lo = fminf(lo, ext);
       hi = fmaxf(hi, ext);
     }
@@ -208,11 +246,14 @@ __device__ __forceinline__ void prepare(const Band& B, float d1, float d2, float
     w1 = min(cellf(fminf(hi, 2.f), half) + mg, lim1);
   }
   const uint32_t wr = range16(w0, w1 + 1);
-  S.cap[0] = rows && bw > 0.f ? wr : 0u;
-  S.cap[1] = rows && !(bw > 0.f) ? wr : 0u;
-  S.cap[2] = !rows && !(bw > 0.f) ? wr : 0u;
-  S.cap[3] = !rows && bw > 0.f ? wr : 0u;
-  S.clip = (uint32_t)B.R0 | ((uint32_t)(B.R1 - 1) << 16);
+  if (ROWS) {
+    S.cap[0] = bw > 0.f ? wr : 0u;
+    S.cap[1] = bw > 0.f ? 0u : wr;
+  } else {
+    S.cap[2] = bw > 0.f ? 0u : wr;
+    S.cap[3] = bw > 0.f ? wr : 0u;
+    S.clip = (uint32_t)(G - 1) << 16;
+  }
 }
 
 // Raw p and q of pair i.
@@ -346,15 +387,15 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   if (ROWS) {
     w.cl = 0;
     w.cr = G - 1;
-    w.ub = B.rt + 4u * (uint32_t)(((m - B.R0) >> 1) * G);
+    w.ub = B.tb + 4u * (uint32_t)(((m - B.R0) >> 1) * G);
     w.inc = ((m - B.R0) & 1) ? 0x10000u : 1u;
     w.pstep = dm > 0 ? 4 * G : -4 * G;
   } else {
     const uint32_t clip = tab[7 * 32 + k];
     w.cl = (int)(clip & 0xffffu);
     w.cr = (int)(clip >> 16);
-    w.ub = B.ct + 4u * (uint32_t)(m >> 1) - (uint32_t)(2 * G * B.R0);
-    w.inc = (m & 1) ? 0x10000u : 1u;
+    w.ub = B.tb + 4u * (uint32_t)((m - B.C0) >> 1);
+    w.inc = ((m - B.C0) & 1) ? 0x10000u : 1u;
     w.pstep = dm > 0 ? 4 : -4;
   }
   w.trig = dm > 0 ? 1u : 0x10000u;
@@ -370,8 +411,8 @@ template <bool ROWS>
 __device__ __forceinline__ void step_walker(Walker& w, int i, const Band& B, uint32_t dummy) {
   int ln, hn;
   const bool en = line_cells(w, w.y, B.half, ln, hn);
-  const int lim = ROWS ? B.G - 1 : B.R1 - 1;
-  const uint32_t xs = ROWS ? 4u : 2u * (uint32_t)B.G;
+  const int lim = B.G - 1;  // the run axis spans the grid (columns for rows, rows for columns)
+  const uint32_t xs = ROWS ? 4u : 4u * (uint32_t)B.W;
   const int b1 = en ? min(ln, max(hn, -(1 << 30)) - 1) : w.hw;
   const int a2 = en ? hn : (1 << 30);
   const int x1 = max(w.lw, w.cl), y1 = min(b1, w.cr);
@@ -434,80 +475,72 @@ __device__ __forceinline__ int deal_offsets(uint32_t* tab, int lane, bool live, 
   return __shfl_sync(kFull, incl, 31);
 }
 
-__global__ void __launch_bounds__(kRunThreads, 1)
-    k_axis_vote_runs(const VoteItem* __restrict__ items, int n_items, const InstDev* __restrict__ insts,
-                     int* __restrict__ counter, int tile_words) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ int s_item, s_next;
+// One work item: the pairs c0..c1 of a slice voted into the item's tile (ROWS: the row caps of
+// a band of rows; else the column caps of a band of columns), the differences turned into
+// counts and the tile written to the slice's partial of the accumulator (columns 2j and 2j + 1
+// of a row share a word).
+template <bool ROWS>
+__device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, uint32_t* smem, int tile_words,
+                                          int* s_next) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* tab = smem + tile_words + warp * kTab;
   const uint32_t dummy = (uint32_t)__cvta_generic_to_shared(smem + tile_words + kRunWarps * kTab + lane);
+  Band B;
+  B.G = D.G;
+  const int G = B.G, W2 = G >> 1;
+  const int e0 = D.band_row0[I.band], e1 = D.band_row0[I.band + 1];
+  B.R0 = ROWS ? e0 : 0;
+  B.R1 = ROWS ? e1 : G;
+  B.C0 = ROWS ? 0 : e0;
+  B.C1 = ROWS ? G : e1;
+  B.W = (B.C1 - B.C0) >> 1;
+  B.step = 2.0f / (float)G;
+  B.half = 0.5f * (float)G;
+  uint32_t* tile = smem;
+  B.tb = (uint32_t)__cvta_generic_to_shared(tile);
+  const int words = ROWS ? ((B.R1 - B.R0) >> 1) * G : G * B.W;
+  uint4* t4 = reinterpret_cast<uint4*>(tile);
+  for (int x = threadIdx.x; x < (words >> 2); x += blockDim.x) t4[x] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+
+  const float* __restrict__ P = D.Pv;  // device memory, or pinned host memory (see InstDev)
+  const float* __restrict__ Q = D.Qv;
+  const int64_t count = I.c1 - I.c0;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(s_next, 32);
+  base = __shfl_sync(kFull, base, 0);
+  float r[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (base + lane < count) load_pair(P, Q, I.c0 + base + lane, r);
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_item = atomicAdd(counter, 1);
-      s_next = 0;
-    }
-    __syncthreads();
-    const int it = s_item;
-    if (it >= n_items) break;
-    const VoteItem I = items[it];
-    const InstDev& D = insts[I.inst];
-    Band B;
-    B.G = D.G;
-    B.R0 = D.band_row0[I.band];
-    B.R1 = D.band_row0[I.band + 1];
-    B.step = 2.0f / (float)D.G;
-    B.half = 0.5f * (float)D.G;
-    const int G = B.G, W2 = G >> 1, rows = B.R1 - B.R0;
-    // row-difference tile: rows/2 x G words; column-difference tile: rows x G/2 words
-    uint32_t* rowt = smem;
-    uint32_t* colt = smem + rows * W2;
-    B.rt = (uint32_t)__cvta_generic_to_shared(rowt);
-    B.ct = (uint32_t)__cvta_generic_to_shared(colt);
-    const int words = rows * G;  // both tiles
-    uint4* t4 = reinterpret_cast<uint4*>(smem);
-    for (int x = threadIdx.x; x < (words >> 2); x += blockDim.x) t4[x] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-
-    const float* __restrict__ P = D.Pv;  // device memory, or pinned host memory (see InstDev)
-    const float* __restrict__ Q = D.Qv;
-    const int64_t count = I.c1 - I.c0;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&s_next, 32);
-    base = __shfl_sync(kFull, base, 0);
-    float r[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (base + lane < count) load_pair(P, Q, I.c0 + base + lane, r);
-    for (;;) {
-      if (base >= count) break;
-      float e1 = 0.f, e2 = 0.f, e3 = 0.f;
-      const bool live = base + lane < count && circle_from(r, e1, e2, e3);
-      int nbase = 0;
-      if (lane == 0) nbase = atomicAdd(&s_next, 32);
-      nbase = __shfl_sync(kFull, nbase, 0);
-      if (nbase + lane < count) load_pair(P, Q, I.c0 + nbase + lane, r);
-      Prepared S;
-      if (live) {
-        prepare(B, e1, e2, e3, S);
-        store_rec(tab, lane, S);
-      } else {
+    if (base >= count) break;
+    float d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    const bool live = base + lane < count && circle_from(r, d1, d2, d3);
+    int nbase = 0;
+    if (lane == 0) nbase = atomicAdd(s_next, 32);
+    nbase = __shfl_sync(kFull, nbase, 0);
+    if (nbase + lane < count) load_pair(P, Q, I.c0 + nbase + lane, r);
+    Prepared S;
+    if (live) {
+      prepare<ROWS>(B, d1, d2, d3, S);
+      store_rec(tab, lane, S);
+    } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) tab[(3 + c) * 32 + lane] = 0u;
-      }
-      __syncwarp();
-      int total = deal_offsets(tab, lane, live, true);
-      if (total > 0) walk_deal<true>(B, tab, total, lane, dummy);
-      __syncwarp();
-      total = deal_offsets(tab, lane, live, false);
-      if (total > 0) walk_deal<false>(B, tab, total, lane, dummy);
-      __syncwarp();
-      base = nbase;
+      for (int c = 0; c < 4; ++c) tab[(3 + c) * 32 + lane] = 0u;
     }
-    __syncthreads();
+    __syncwarp();
+    const int total = deal_offsets(tab, lane, live, ROWS);
+    if (total > 0) walk_deal<ROWS>(B, tab, total, lane, dummy);
+    __syncwarp();
+    base = nbase;
+  }
+  __syncthreads();
 
-    // differences -> counts: along each row pair of the row tile (a warp per row pair), and
-    // down each word column of the column tile (a thread per word column)
-    for (int rp = warp; rp < (rows >> 1); rp += kRunWarps) {
-      uint32_t* row = rowt + rp * G;
+  uint4* out4 = reinterpret_cast<uint4*>(D.partial + (int64_t)I.slice * G * W2);
+  if (ROWS) {
+    // prefix sums along each row pair (a warp per row pair), then each row's counters in
+    // column pairs
+    for (int rp = warp; rp < ((B.R1 - B.R0) >> 1); rp += kRunWarps) {
+      uint32_t* row = tile + rp * G;
       uint32_t carry = 0;
       for (int c0 = 0; c0 < G; c0 += 32) {
         const int c = c0 + lane;
@@ -522,30 +555,68 @@ __global__ void __launch_bounds__(kRunThreads, 1)
         carry = __shfl_sync(kFull, v, 31);
       }
     }
-    for (int c2 = threadIdx.x; c2 < W2; c2 += blockDim.x) {
-      uint32_t acc = 0;
-      for (int rr = 0; rr < rows; ++rr) {
-        acc += colt[rr * W2 + c2];
-        colt[rr * W2 + c2] = acc;
-      }
-    }
     __syncthreads();
-
-    // the band -> this slice's partial (columns 2j and 2j + 1 share a word): the column tile's
-    // word plus the two row-tile counters of the same cells
-    uint4* out = reinterpret_cast<uint4*>(D.partial + ((int64_t)I.slice * G + B.R0) * W2);
-    const uint4* c4 = reinterpret_cast<const uint4*>(colt);
-    for (int g = threadIdx.x; g < ((rows * W2) >> 2); g += blockDim.x) {
+    for (int g = threadIdx.x; g < (((B.R1 - B.R0) * W2) >> 2); g += blockDim.x) {
       const int rr = (4 * g) / W2, c2 = 4 * g - rr * W2;
-      const uint4 cwv = c4[g];
-      const uint4* rw = reinterpret_cast<const uint4*>(rowt + (rr >> 1) * G + 2 * c2);
+      const uint4* rw = reinterpret_cast<const uint4*>(tile + (rr >> 1) * G + 2 * c2);
       const uint4 ra = rw[0], rb = rw[1];
       const int sh = (rr & 1) ? 16 : 0;
       auto pk = [sh](uint32_t x, uint32_t y) { return ((x >> sh) & 0xffffu) | (((y >> sh) & 0xffffu) << 16); };
-      out[g] = make_uint4(cwv.x + pk(ra.x, ra.y), cwv.y + pk(ra.z, ra.w), cwv.z + pk(rb.x, rb.y),
-                          cwv.w + pk(rb.z, rb.w));
+      out4[((B.R0 + rr) * W2 + c2) >> 2] = make_uint4(pk(ra.x, ra.y), pk(ra.z, ra.w), pk(rb.x, rb.y), pk(rb.z, rb.w));
+    }
+  } else {
+    // prefix sums down each word column in chunks of rows (a thread per column and chunk), the
+    // chunks' carries, then the rows
+    const int W = B.W;
+    const int nch = max(1, min((int)blockDim.x / W, G / 8));
+    const int rpc = (G + nch - 1) / nch;
+    if ((int)threadIdx.x < W * nch) {
+      const int c2 = threadIdx.x % W, ch = threadIdx.x / W;
+      const int r1 = min(G, (ch + 1) * rpc);
+      uint32_t acc = 0;
+      for (int rr = ch * rpc; rr < r1; ++rr) {
+        acc += tile[rr * W + c2];
+        tile[rr * W + c2] = acc;
+      }
     }
     __syncthreads();
+    uint32_t* carry = smem + tile_words;  // the tables' space, free after the walk
+    if ((int)threadIdx.x < W * nch) {
+      const int c2 = threadIdx.x % W, ch = threadIdx.x / W;
+      uint32_t c = 0;
+      for (int k = 0; k < ch; ++k) c += tile[(min(G, (k + 1) * rpc) - 1) * W + c2];
+      carry[ch * W + c2] = c;
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < ((G * W) >> 2); g += blockDim.x) {
+      const int rr = (4 * g) / W, c2 = 4 * g - rr * W;
+      const uint4 v = reinterpret_cast<const uint4*>(tile)[g];
+      const uint4 c = *reinterpret_cast<const uint4*>(carry + (rr / rpc) * W + c2);
+      out4[(rr * W2 + (B.C0 >> 1) + c2) >> 2] = make_uint4(v.x + c.x, v.y + c.y, v.z + c.z, v.w + c.w);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kRunThreads, 1)
+    k_axis_vote_runs(const VoteItem* __restrict__ items, int n_items, const InstDev* __restrict__ insts,
+                     int* __restrict__ counter, int tile_words) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_item, s_next;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(counter, 1);
+      s_next = 0;
+    }
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const VoteItem I = items[it];
+    const InstDev& D = insts[I.inst];
+    if (I.kind == 0)
+      vote_item<true>(I, D, smem, tile_words, &s_next);
+    else
+      vote_item<false>(I, D, smem, tile_words, &s_next);
   }
 }
 

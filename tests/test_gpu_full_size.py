@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 
 
 def test_band_seam_rows_at_full_size(lib):
+    """Whole rows and columns at every band seam (the vote clips the curve's row caps to bands of
+    rows and its column caps to bands of columns with the same edges), the first and last rows,
+    and the peak row. A column of the accumulator of (P, Q) is the row of the accumulator of the
+    pairs with their first two coordinates exchanged (F is symmetric in (u, d1) and (v, d2))."""
     from paper_2502_06337_gb300 import binding as B
 
     cfg = synth.HEADLINE
@@ -28,12 +32,15 @@ def test_band_seam_rows_at_full_size(lib):
     seams = plan["band_row0"][1:-1]
     assert len(seams) >= 1
     rows = sorted({0, G - 1, g["rots"][0]["cell"][0]} | {r for s in seams for r in (s - 1, s)})
+    cols = sorted({c for s in seams for c in (s - 1, s)})
+    swap = [1, 0, 2]
+    lines = [(g["grid"][r], prob.P, prob.Q, r) for r in rows] + \
+            [(g["grid"][:, c], prob.P[:, swap], prob.Q[:, swap], c) for c in cols]
     width = []
-    for row in rows:
-        cnt, lo, hi = oracle.row_votes(prob.P, prob.Q, G, row)
-        got = g["grid"][row]
-        assert np.all(got >= lo) and np.all(got <= hi), row
-        assert np.all(got[lo == hi] == cnt[lo == hi]), row
+    for got, P, Q, k in lines:
+        cnt, lo, hi = oracle.row_votes(P, Q, G, k)
+        assert np.all(got >= lo) and np.all(got <= hi), k
+        assert np.all(got[lo == hi] == cnt[lo == hi]), k
         width.append(hi - lo)
     # with 10^6 circles most cells have some circle within the band, but only a few: the
     # bounds stay tight (a few votes wide against thousands per cell)
