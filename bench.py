@@ -161,7 +161,7 @@ def vote_profile():
     """The committed ncu record of the axis-vote kernel (DRAM bytes and warp instructions per
     launch), or {} when the kernel source has changed since the counters were taken."""
     prof = os.path.join(ROOT, "profiles", "axis_vote_traffic.json")
-    src = os.path.join(ROOT, "paper_2502_06337_gb300", "csrc", "vote_walk.cu")
+    src = os.path.join(ROOT, "paper_2502_06337_gb300", "csrc", "vote_runs.cu")
     try:
         rec = json.load(open(prof))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -267,8 +267,8 @@ def run_sprot(args):
     achieved = increments / vote_s
     roofline = {
         "bound": "alu",
-        "resource": "shared-memory atomic unit (red.shared.add.u32 per voted cell)",
-        "kernel": "k_axis_vote_walk",
+        "resource": "shared-memory atomic unit (the rate of one red.shared.add.u32 per voted cell)",
+        "kernel": "k_axis_vote_runs",
         "achieved": achieved / 1e9,
         "peak": atomic_peak / 1e9,
         "unit": "Gatom/s",

@@ -128,61 +128,71 @@ __device__ void finalize_instance(const InstDev& D) {
   *D.n_found = found;
 }
 
-__global__ void __launch_bounds__(kReduceWords / 4)
+// Sum of the slice partials over an item of accumulator words, 128 words (256 cells) at a time:
+// the block's 8 warps take every 8th slice, each lane one 16-byte column of 4 words (the loads
+// of a lane's slices are independent and issued together), then each thread adds one cell over
+// the 8 warps' sums, writes it to the grid and keeps the largest peak key.
+constexpr int kReduceThreads = 256;
+constexpr int kReduceGroups = kReduceThreads / 32;
+__global__ void __launch_bounds__(kReduceThreads)
     k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  __shared__ uint32_t part[kReduceGroups][256];
   const ReduceItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   const int G = D.G, W = G >> 1, S = D.S;
-  const int64_t plane = (int64_t)G * W;
+  const int64_t stride = (int64_t)G * W / 4;  // uint4 per slice
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   unsigned long long best = 0;
-  // words w .. w+3 lie in one row (W % 4 == 0); an item may span several passes of the block
-  for (int64_t w = I.w0 + 4 * threadIdx.x; w < I.w1; w += 4 * blockDim.x) {
+  for (int64_t w0 = I.w0; w0 < I.w1; w0 += 128) {
+    const int64_t w = w0 + 4 * lane;  // words w .. w+3 (W % 4 == 0: one row)
     uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint4* p = reinterpret_cast<const uint4*>(D.partial + w);
-    const int64_t stride = plane / 4;
-    int s = 0;
-    for (; s + 4 <= S; s += 4) {
-      uint4 v[4];
+    if (w < I.w1) {
+      const uint4* p = reinterpret_cast<const uint4*>(D.partial + w);
+      int s = grp;
+      for (; s + 3 * kReduceGroups < S; s += 4 * kReduceGroups) {
+        uint4 v[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) v[t] = __ldcs(p + (s + t) * stride);
+        for (int t = 0; t < 4; ++t) v[t] = __ldcs(p + (s + t * kReduceGroups) * stride);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        c[0] += v[t].x & 0xffffu;
-        c[1] += v[t].x >> 16;
-        c[2] += v[t].y & 0xffffu;
-        c[3] += v[t].y >> 16;
-        c[4] += v[t].z & 0xffffu;
-        c[5] += v[t].z >> 16;
-        c[6] += v[t].w & 0xffffu;
-        c[7] += v[t].w >> 16;
+        for (int t = 0; t < 4; ++t) {
+          c[0] += v[t].x & 0xffffu;
+          c[1] += v[t].x >> 16;
+          c[2] += v[t].y & 0xffffu;
+          c[3] += v[t].y >> 16;
+          c[4] += v[t].z & 0xffffu;
+          c[5] += v[t].z >> 16;
+          c[6] += v[t].w & 0xffffu;
+          c[7] += v[t].w >> 16;
+        }
+      }
+      for (; s < S; s += kReduceGroups) {
+        const uint4 v = __ldcs(p + s * stride);
+        c[0] += v.x & 0xffffu;
+        c[1] += v.x >> 16;
+        c[2] += v.y & 0xffffu;
+        c[3] += v.y >> 16;
+        c[4] += v.z & 0xffffu;
+        c[5] += v.z >> 16;
+        c[6] += v.w & 0xffffu;
+        c[7] += v.w >> 16;
       }
     }
-    for (; s < S; ++s) {
-      const uint4 v = __ldcs(p + s * stride);
-      c[0] += v.x & 0xffffu;
-      c[1] += v.x >> 16;
-      c[2] += v.y & 0xffffu;
-      c[3] += v.y >> 16;
-      c[4] += v.z & 0xffffu;
-      c[5] += v.z >> 16;
-      c[6] += v.w & 0xffffu;
-      c[7] += v.w >> 16;
-    }
-    // word j of a row holds columns 2j (low half) and 2j + 1 (high half)
-    const int row = (int)(w / W), col = 2 * (int)(w - (int64_t)row * W);
-    uint32_t* g = D.grid + (int64_t)row * G + col;
-    if ((reinterpret_cast<uintptr_t>(g) & 15u) == 0) {
-      reinterpret_cast<uint4*>(g)[0] = make_uint4(c[0], c[1], c[2], c[3]);
-      reinterpret_cast<uint4*>(g)[1] = make_uint4(c[4], c[5], c[6], c[7]);
-    } else {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) g[t] = c[t];
-    }
+    for (int t = 0; t < 8; ++t) part[grp][8 * lane + t] = c[t];
+    __syncthreads();
+    // cell t of the chunk: word w0 + t/2, column half t&1
+    const int t = threadIdx.x;
+    const int64_t wc = w0 + (t >> 1);
+    if (wc < I.w1) {
+      uint32_t v = 0;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const unsigned long long k = peak_key(c[t], (uint32_t)(row * G + col + t));
+      for (int g = 0; g < kReduceGroups; ++g) v += part[g][t];
+      const int row = (int)(wc / W), col = 2 * (int)(wc - (int64_t)row * W) + (t & 1);
+      D.grid[(int64_t)row * G + col] = v;
+      const unsigned long long k = peak_key(v, (uint32_t)(row * G + col));
       best = k > best ? k : best;
     }
+    __syncthreads();
   }
   best = block_max_u64(best);
   if (threadIdx.x == 0 && best) atomicMax(&D.peak_key[0], best);
@@ -296,15 +306,26 @@ struct PairGeom {
   bool deg;
 };
 
-__device__ __forceinline__ void load_pair(const InstDev& D, int64_t i, PairGeom& g) {
+// Raw p and q of pair i (six loads, independent of one another).
+__device__ __forceinline__ void load_raw(const InstDev& D, int64_t i, float* r) {
   const float* p = D.P + 3 * i;
   const float* q = D.Q + 3 * i;
-  g.p0 = __ldg(p);
-  g.p1 = __ldg(p + 1);
-  g.p2 = __ldg(p + 2);
-  g.q0 = __ldg(q);
-  g.q1 = __ldg(q + 1);
-  g.q2 = __ldg(q + 2);
+  r[0] = __ldg(p);
+  r[1] = __ldg(p + 1);
+  r[2] = __ldg(p + 2);
+  r[3] = __ldg(q);
+  r[4] = __ldg(q + 1);
+  r[5] = __ldg(q + 2);
+}
+
+// The pair's points and its scaled difference p - q.
+__device__ __forceinline__ void pair_geom(const float* r, PairGeom& g) {
+  g.p0 = r[0];
+  g.p1 = r[1];
+  g.p2 = r[2];
+  g.q0 = r[3];
+  g.q1 = r[4];
+  g.q2 = r[5];
   float d1 = g.p0 - g.q0, d2 = g.p1 - g.q1, d3 = g.p2 - g.q2;
   float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
   g.deg = (m == 0.f);
@@ -371,9 +392,17 @@ __global__ void __launch_bounds__(kStreamThreads)
   const float scale = (float)J / two_pi;
   const float pi_f = 3.14159265358979f;
   unsigned ndeg = 0;
+  // each thread's pairs i, i + blockDim, ...: the next pair's loads are issued before the
+  // current pair is processed
+  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (I.i0 + threadIdx.x < I.i1) load_raw(D, I.i0 + threadIdx.x, nx);
   for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
+    float cur[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) cur[t] = nx[t];
+    if (i + blockDim.x < I.i1) load_raw(D, i + blockDim.x, nx);
     PairGeom g;
-    load_pair(D, i, g);
+    pair_geom(cur, g);
     ndeg += g.deg;
     float pp = fmaf(g.p0, g.p0, fmaf(g.p1, g.p1, g.p2 * g.p2));
     float qq = fmaf(g.q0, g.q0, fmaf(g.q1, g.q1, g.q2 * g.q2));
@@ -615,13 +644,21 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   PairQueues<K> pq;
   pq.init(queues[wp]);
   const float tau2 = D.tau * D.tau;
+  // each warp takes 32 consecutive pairs per iteration; the next iteration's loads are issued
+  // before the current pairs are processed
+  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (I.i0 + 32 * wp + lane < I.i1) load_raw(D, I.i0 + 32 * wp + lane, nx);
   for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
     const int64_t i = base + lane;
     const bool valid = i < I.i1;
+    float cur[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) cur[t] = nx[t];
+    if (i + blockDim.x < I.i1) load_raw(D, i + blockDim.x, nx);
     int lab = -1;
     if (valid) {
-      const float p0 = __ldg(D.P + 3 * i), p1 = __ldg(D.P + 3 * i + 1), p2 = __ldg(D.P + 3 * i + 2);
-      const float q0 = __ldg(D.Q + 3 * i), q1 = __ldg(D.Q + 3 * i + 1), q2 = __ldg(D.Q + 3 * i + 2);
+      const float p0 = cur[0], p1 = cur[1], p2 = cur[2];
+      const float q0 = cur[3], q1 = cur[4], q2 = cur[5];
       float best = CUDART_INF_F;
       for (int a = 0; a < kf; ++a) {
         const float* R = Rf[a];
@@ -1153,7 +1190,7 @@ void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, 
 
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st) {
-  k_grid_reduce<<<n_items, kReduceWords / 4, 0, st>>>(items, insts);
+  k_grid_reduce<<<n_items, kReduceThreads, 0, st>>>(items, insts);
   launches_add(1);
 }
 

@@ -474,7 +474,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     int64_t words = (int64_t)ip.G * (ip.G / 2);
     const int64_t red_words =
         m == 1 ? kReduceWords
-               : kReduceWords * std::min<int64_t>(16, std::max<int64_t>(1, 64 / std::max(ip.S, 1)));
+               : kReduceWords * std::min<int64_t>(64, std::max<int64_t>(1, 256 / std::max(ip.S, 1)));
     const size_t r0 = ritems.size();
     for (int64_t w0 = 0; w0 < words; w0 += red_words)
       ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + red_words, words)});

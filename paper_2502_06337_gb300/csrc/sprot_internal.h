@@ -14,7 +14,7 @@ constexpr int kMaxK = SPROT_MAX_K;
 constexpr int kMaxBands = SPROT_MAX_BANDS;  // row bands of one accumulator (G = 2048 needs 94)
 constexpr int kStreamThreads = 256;  // threads of the per-pair kernels
 constexpr int kStreamChunk = 8192;   // pairs per per-pair work item
-constexpr int kReduceWords = 512;   // accumulator words per slice-reduction item (128 x uint4)
+constexpr int kReduceWords = 128;   // accumulator words per slice-reduction item (32 x uint4)
 constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // tile; leaves room for static shared
 constexpr int kRunSmemBytes = 227 * 1024 - 64;    // the curve vote's tiles and tables (16 B static)
 constexpr int kMaxSliceCircles = 65535;  // u16 tile counters: at most this many circles/slice
