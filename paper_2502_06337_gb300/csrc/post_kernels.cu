@@ -885,6 +885,55 @@ __device__ bool polar_start_f32(const double* Xd, double* q) {
   return true;
 }
 
+// Polar factor of X (det X > 0, entries of order 1) from the unit quaternion q0 of a nearby
+// rotation, in float32: the Cayley steps of the FP64 refinement below (the symmetric part H of
+// U^T X, the solve (tr(H) I - H) w = v for the antisymmetric residual v, q <- q (1, w/2)) carried
+// out entirely in float32. Each step squares the error until float32 rounding (about 1e-7)
+// limits it; from a start within a few degrees three steps reach it. Returns false (q not
+// written) if the system is not positive definite or the steps do not settle.
+__device__ bool polar_cayley_f32(const double* Xd, const float* q0, double* q) {
+  float X[9];
+  for (int t = 0; t < 9; ++t) X[t] = (float)Xd[t];
+  float a = q0[0], b = q0[1], c = q0[2], d = q0[3];
+  float n2 = 1.f;
+  int it = 0;
+  for (; it < 8 && n2 >= 1e-13f; ++it) {
+    // U = |q|^2 x the rotation of q
+    const float U[9] = {a * a + b * b - c * c - d * d, 2.f * (b * c - a * d), 2.f * (b * d + a * c),
+                        2.f * (b * c + a * d), a * a - b * b + c * c - d * d, 2.f * (c * d - a * b),
+                        2.f * (b * d - a * c), 2.f * (c * d + a * b), a * a - b * b - c * c + d * d};
+    float Y[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Y[3 * i + j] = fmaf(U[i], X[j], fmaf(U[3 + i], X[3 + j], U[6 + i] * X[6 + j]));
+    const float v0 = Y[7] - Y[5], v1 = Y[2] - Y[6], v2 = Y[3] - Y[1];
+    const float a00 = Y[4] + Y[8], a11 = Y[0] + Y[8], a22 = Y[0] + Y[4];
+    const float a01 = -0.5f * (Y[1] + Y[3]), a02 = -0.5f * (Y[2] + Y[6]), a12 = -0.5f * (Y[5] + Y[7]);
+    const float c00 = a11 * a22 - a12 * a12, c11 = a00 * a22 - a02 * a02, c22 = a00 * a11 - a01 * a01;
+    const float c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11, c12 = a01 * a02 - a00 * a12;
+    const float det = a00 * c00 + a01 * c01 + a02 * c02;
+    if (!(det > 0.f) || !(a00 > 0.f)) return false;
+    const float inv = 0.5f * __frcp_rn(det);  // half of w: the Cayley vector
+    const float w0 = (c00 * v0 + c01 * v1 + c02 * v2) * inv;
+    const float w1 = (c01 * v0 + c11 * v1 + c12 * v2) * inv;
+    const float w2 = (c02 * v0 + c12 * v1 + c22 * v2) * inv;
+    n2 = w0 * w0 + w1 * w1 + w2 * w2;
+    const float na = a - b * w0 - c * w1 - d * w2, nb = a * w0 + b + c * w2 - d * w1;
+    const float nc = a * w1 - b * w2 + c + d * w0, nd = a * w2 + b * w1 - c * w0 + d;
+    // renormalise (the step scales |q| by sqrt(1 + |w|^2))
+    const float rn = rsqrtf(na * na + nb * nb + nc * nc + nd * nd);
+    a = na * rn;
+    b = nb * rn;
+    c = nc * rn;
+    d = nd * rn;
+  }
+  if (!(n2 < 1e-10f)) return false;
+  q[0] = a;
+  q[1] = b;
+  q[2] = c;
+  q[3] = d;
+  return true;
+}
+
 // Polar factor of X (det X > 0) refined from the quaternion q of a nearby rotation U. The
 // polar factor is the rotation U with U^T X symmetric. Writing the correction as U exp([w]x)
 // and keeping first-order terms, with Y = U^T X and H its symmetric part,
@@ -946,6 +995,42 @@ __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
 // FP64 operation costs tens of cycles on this part, so the chains are kept short: the
 // singularity test needs no square root and X is M scaled by a power of two (the polar factor
 // does not depend on the scale).
+// Unit quaternion (w, x, y, z) of a rotation matrix, row-major, by Shepperd's method (the
+// largest of the trace and the diagonal picks the stable formula); float32 output.
+__device__ void rot_to_quat(const double* M, float* q) {
+  const double tr = M[0] + M[4] + M[8];
+  double w, x, y, z;
+  if (tr >= M[0] && tr >= M[4] && tr >= M[8]) {
+    w = 0.5 * sqrt(fmax(1.0 + tr, 0.0));
+    const double f = 0.25 / w;
+    x = (M[7] - M[5]) * f;
+    y = (M[2] - M[6]) * f;
+    z = (M[3] - M[1]) * f;
+  } else if (M[0] >= M[4] && M[0] >= M[8]) {
+    x = 0.5 * sqrt(fmax(1.0 + M[0] - M[4] - M[8], 0.0));
+    const double f = 0.25 / x;
+    w = (M[7] - M[5]) * f;
+    y = (M[1] + M[3]) * f;
+    z = (M[2] + M[6]) * f;
+  } else if (M[4] >= M[8]) {
+    y = 0.5 * sqrt(fmax(1.0 - M[0] + M[4] - M[8], 0.0));
+    const double f = 0.25 / y;
+    w = (M[2] - M[6]) * f;
+    x = (M[1] + M[3]) * f;
+    z = (M[5] + M[7]) * f;
+  } else {
+    z = 0.5 * sqrt(fmax(1.0 - M[0] - M[4] + M[8], 0.0));
+    const double f = 0.25 / z;
+    w = (M[3] - M[1]) * f;
+    x = (M[2] + M[6]) * f;
+    y = (M[5] + M[7]) * f;
+  }
+  q[0] = (float)w;
+  q[1] = (float)x;
+  q[2] = (float)y;
+  q[3] = (float)z;
+}
+
 // The FP64 rotation of rotation a from its ten sums (M = sum q p^T and the count): the polar
 // factor of M (float32 start, FP64 refinement), with the Jacobi fallbacks for reflecting or
 // rank-deficient sums. One thread.
@@ -955,6 +1040,7 @@ __device__ void solve_rotation(const InstDev& D, int a, int phase, const double*
   for (int t = 0; t < 10; ++t) s[t] = tot[t];
   DevRot& R = D.rot[a];
   double out[9];
+  bool q_set = false;  // R.q_init written from the refined quaternion
   const uint32_t cnt = (uint32_t)s[9];
   if (cnt == 0) {
     const double* fb = phase == 0 ? R.R_vote : R.R_init;
@@ -973,8 +1059,26 @@ __device__ void solve_rotation(const InstDev& D, int a, int phase, const double*
     double X[9];
     for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
     double q[4];
+    // the start: the nearby rotation the previous stage found (R_vote for the vote set, R_init for
+    // the inliers), carried to float32 precision by float32 Cayley steps; the scaled Newton
+    // iteration when those do not settle
+    float q0[4];
+    if (phase == 0) {
+      float sh, ch;
+      sincosf(0.5f * (float)R.theta, &sh, &ch);
+      q0[0] = ch;
+      q0[1] = sh * (float)R.axis[0];
+      q0[2] = sh * (float)R.axis[1];
+      q0[3] = sh * (float)R.axis[2];
+    } else {
+      for (int t = 0; t < 4; ++t) q0[t] = R.q_init[t];
+    }
     const bool ok = det > 0.0 && det * det > 1e-18 * (n2 * n2 * n2) && e > -1000 && e < 1000 &&
-                    polar_start_f32(X, q) && polar_refine_f64(X, q, out);
+                    (polar_cayley_f32(X, q0, q) || polar_start_f32(X, q)) && polar_refine_f64(X, q, out);
+    if (ok && phase == 0) {
+      for (int t = 0; t < 4; ++t) R.q_init[t] = (float)q[t];
+      q_set = true;
+    }
     if (!ok && !polar_rotation(s, out)) horn_rotation(s, out);  // reflecting or rank-deficient sums
   }
   if (phase == 0) {
@@ -983,6 +1087,7 @@ __device__ void solve_rotation(const InstDev& D, int a, int phase, const double*
       R.R_init_f[t] = (float)out[t];
     }
     R.n_vote_set = cnt;
+    if (!q_set) rot_to_quat(out, R.q_init);
   } else {
     for (int t = 0; t < 9; ++t) R.R[t] = out[t];
     R.n_inliers = cnt;

@@ -31,6 +31,7 @@ struct DevRot {
   int32_t cell_row, cell_col, angle_bin;
   uint32_t axis_votes, angle_votes, n_vote_set, n_inliers, n_degenerate;
   double cell_offset[2];  // sub-cell peak offset (u, v) in cells
+  float q_init[4];        // unit quaternion of R_init (w, x, y, z): the start of the second solve
 };
 
 // One problem of a (possibly single-element) batch, as the kernels see it.
