@@ -326,6 +326,10 @@ def run_sprot(args):
             except Exception as e:
                 out["sampled_vote"] = {"error": repr(e)}
             try:
+                out["eps_vote"] = run_eps(B, P, Q, G)
+            except Exception as e:
+                out["eps_vote"] = {"error": repr(e)}
+            try:
                 out["batched"] = run_batched(B, dev)
             except Exception as e:  # report, never hide
                 out["batched"] = {"error": repr(e)}
@@ -567,6 +571,30 @@ def run_sampled(B, P, Q, G, J=360, reps=5):
     return {"points_per_circle": J, "grid": G, "ms": ms, "Mcorr_per_s": n / ms / 1e3,
             "Gpoints_per_s": n * J / ms / 1e6, "votes": votes, "Gvotes_per_s": votes / ms / 1e6,
             "note": "L2 atomics (red.global.add) into the grid; inputs L2-warm"}
+
+
+def run_eps(B, P, Q, G, reps=5):
+    """The eps-band accumulator of Eq. 9 (sprot_axis_vote_eps: vote and slice reduction into a
+    caller grid) on the headline pairs at eps = 0, 0.002 and 0.01."""
+    import torch
+
+    n = P.shape[0]
+    grid = torch.zeros(G * G, dtype=torch.int32, device=P.device)
+    st = torch.cuda.current_stream()
+    out = {"workload": f"n={n} headline pairs, {G}^2", "grid": G}
+    for eps in (0.0, 0.002, 0.01):
+        B.axis_vote_eps(P, Q, G, eps, grid)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            B.axis_vote_eps(P, Q, G, eps, grid)
+        b.record(st)
+        torch.cuda.synchronize()
+        votes = int(grid.cpu().numpy().view(np.uint32).astype(np.int64).sum())
+        out[f"eps={eps:g}"] = {"ms_per_call": a.elapsed_time(b) / reps, "votes": votes}
+    out["note"] = "each call uploads its work table, votes, reduces and synchronizes its stream"
+    return out
 
 
 def run_batched(B, dev, m=4096, loop_sample=512):

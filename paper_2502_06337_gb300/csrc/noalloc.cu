@@ -82,7 +82,10 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SPROT_E_CUDA;
   int T = 0, S = 0, tile = 0, nsm = 0;
   NoallocSetup s{};
-  if (!single_vote_plan(n, G, dev, &T, s.inst.band_row0, &S, &tile, &nsm)) return SPROT_E_INVAL;
+  // at most the slices whose partials (4 G^2 bytes a slice) fit the scratch beside 2 MB of tables
+  const int64_t cap = ((int64_t)SPROT_NOALLOC_SCRATCH_BYTES - (2 << 20)) / (4 * (int64_t)G * G);
+  if (!single_vote_plan(n, G, dev, &T, s.inst.band_row0, &S, &tile, &nsm, std::max<int64_t>(cap, 1)))
+    return SPROT_E_INVAL;
   const int n_items = 2 * T * S;
   const int64_t words = (int64_t)G * (G / 2);
   const int n_ritems = (int)((words + kReduceWords - 1) / kReduceWords);

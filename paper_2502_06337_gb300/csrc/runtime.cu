@@ -325,7 +325,8 @@ int batch_chunk(int64_t total) {
 // Vote layout of one instance: row bands that fit the shared tile, and circle slices (at most
 // 65535 circles each, so the 16-bit counters cannot overflow). A single problem is spread
 // over every SM; in a batch each instance gets slices of 32768 circles.
-void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false) {
+void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false,
+               int64_t max_slices = INT64_MAX) {
   if (eps)
     plan_bands(ip.G, kMaxSmemBytes, eps_row_bytes(ip.G), 0, &ip.T, ip.row0);
   else
@@ -334,7 +335,15 @@ void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false) 
   // the curve vote has 2 T items per slice (row bands and column bands), the eps-band vote T
   const int per_slice = (eps ? 1 : 2) * std::max(ip.T, 1);
   int64_t s = single ? std::max<int64_t>(1, nsm / per_slice) : (n + 32767) / 32768;
+  if (single && s < s_min) {
+    // the counters force more slices than one round of the SMs holds: the most slices whose
+    // items fill whole rounds (k rounds, k * nsm >= s_min * per_slice), so that no round runs
+    // with most SMs idle
+    const int64_t k = (s_min * per_slice + nsm - 1) / nsm;
+    s = k * nsm / per_slice;
+  }
   s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
+  s = std::min<int64_t>(s, max_slices);
   ip.S = (int)std::max(s, s_min);
 }
 
@@ -346,11 +355,12 @@ int tile_bytes(const InstPlan& ip, bool eps = false) {
 
 }  // namespace
 
-bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm) {
+bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm,
+                      int64_t max_slices) {
   InstPlan ip{};
   ip.G = G;
   *nsm = sm_count(dev);
-  plan_vote(ip, n, true, *nsm);
+  plan_vote(ip, n, true, *nsm, false, max_slices);
   if (ip.T <= 0) return false;
   *T = ip.T;
   for (int b = 0; b <= ip.T; ++b) row0[b] = ip.row0[b];

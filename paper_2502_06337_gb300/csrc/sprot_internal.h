@@ -109,7 +109,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true);
 
 // The axis-vote plan of a single solve of n pairs on a G x G grid on device dev: T row bands
 // (row0[T + 1]), S circle slices, the largest band tile in bytes and the device's SM count.
-bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm);
+bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, int* tile, int* nsm,
+                      int64_t max_slices = INT64_MAX);
 
 // Frees the solve() workspace of stream st (call before destroying st).
 void release_workspace(cudaStream_t st);

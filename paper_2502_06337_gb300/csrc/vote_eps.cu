@@ -8,17 +8,24 @@
 // (m = min of the F_minus part, M = max of the F_plus part), and the cell of column c meets
 // the band iff [u_c, u_c+1] meets S1 = {u : Cm u^2 + 2 d1 u + m < 0} and meets
 // S2 = {u : Cp u^2 + 2 d1 u + M > 0}, Cm/Cp = d3 -/+ eps |d|. Each set is at most two open
-// intervals, so a row votes at most four disjoint column ranges. One warp takes one circle;
-// its lanes take consecutive rows of the band (neighbouring rows have similar spans). Votes go
-// to the same shared band tiles (two u16 counters per word) and slice partials as the curve
-// vote, and the same reduction sums them.
+// intervals, so a row votes at most four disjoint column ranges.
+//
+// Work split. One warp takes one circle; its lanes take consecutive rows of the band, limited to
+// the rows of the disc {F_minus < 0} when that set is a disc (d scaled by a power of two and
+// signed so that d3 >= 0; then F_plus's quadratic term d3 + eps |d| is positive and
+// {F_plus > 0} is the outside of a disc or a half-plane, met on every row). A row's ranges are
+// entered as differences (+1 at a range's first column, -1 after its last) into a shared tile of
+// row pairs, so a row costs its quadratics and at most eight atomics however long its ranges
+// are. After the slice, prefix sums along the rows turn the tile into counts, which go to the
+// slice's partial of the accumulator; the reduction of the curve vote sums the slices.
+#include "row_tiles.cuh"
 #include "sprot_internal.h"
 
 namespace sprot {
 
 namespace {
 
-constexpr int kEpsThreads = 512;
+constexpr int kEpsThreads = 1024;
 
 struct Ranges {
   int a[2], b[2];  // closed column ranges, sorted and disjoint; empty when a > b
@@ -39,6 +46,29 @@ __device__ __forceinline__ void cols_meeting(float lo, float hi, float half, int
 __device__ __forceinline__ void roots2(float inv_c, float b, float k, float disc, float& r1, float& r2) {
   const float q = -(b + copysignf(sqrtf(disc), b));
   const float x = q * inv_c, y = k * __frcp_rn(q);
+  r1 = fminf(x, y);
+  r2 = fmaxf(x, y);
+}
+
+// Hardware approximations (flush to zero): reciprocal square root and reciprocal, a few ulp.
+__device__ __forceinline__ float rsqrt_apx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_apx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ int clampi(int x, int G) { return min(max(x, 0), G); }
+
+// roots2 through the approximations, for disc > 1e-30 (so that the square root is a normal
+// number and q cannot vanish).
+__device__ __forceinline__ void roots2_apx(float inv_c, float b, float k, float disc, float& r1, float& r2) {
+  const float q = -(b + copysignf(disc * rsqrt_apx(disc), b));
+  const float x = q * inv_c, y = k * rcp_apx(q);
   r1 = fminf(x, y);
   r2 = fmaxf(x, y);
 }
@@ -116,20 +146,13 @@ __device__ __forceinline__ Ranges cell_ranges(float c, float inv_c, float b, flo
   return R;
 }
 
-// Adds one to the cells of row `row` (relative to the tile) in columns [a, b]; two adjacent
-// columns share a word (low half even, high half odd).
-__device__ __forceinline__ void vote_span(uint32_t sbase, int W, int row, int a, int b) {
+// Enters the run of columns [a, b] of one row as a difference at the row's tile address
+// rowbase (inc = 1 for the first row of a pair, 2^16 for the second).
+__device__ __forceinline__ void vote_run(uint32_t rowbase, uint32_t inc, int G, int a, int b) {
   if (a > b) return;
-  uint32_t addr = sbase + 4u * (uint32_t)(row * W + (a >> 1));
-  int c = a;
-  if (c & 1) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(0x10000u) : "memory");
-    addr += 4;
-    ++c;
-  }
-  for (; c + 1 <= b; c += 2, addr += 4)
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(0x10001u) : "memory");
-  if (c == b) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(1u) : "memory");
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(rowbase + 4u * (uint32_t)a), "r"(inc) : "memory");
+  if (b + 1 < G)
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(rowbase + 4u * (uint32_t)(b + 1)), "r"(0u - inc) : "memory");
 }
 
 // min (lo) or max (!lo) of c v^2 + 2 b v over [v0, v1] (inv_c = 1/c): the ends, and the
@@ -158,11 +181,11 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
     if (it >= n_items) break;
     const VoteItem I = items[it];
     const InstDev& D = insts[I.inst];
-    const int G = D.G, W = G >> 1;
+    const int G = D.G;
     const int R0 = D.band_row0[I.band], R1 = D.band_row0[I.band + 1];
     const float step = 2.0f / (float)G, half = 0.5f * (float)G;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
-    const int words = (R1 - R0) * W;
+    const int words = ((R1 - R0) >> 1) * G;
     uint4* t4 = reinterpret_cast<uint4*>(tile);
     for (int w = threadIdx.x; w < (words >> 2); w += blockDim.x) t4[w] = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -173,27 +196,83 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
       const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
       if (m == 0.f) continue;  // degenerate: no circle
       const int e = ilogbf(m);
-      d1 = scalbnf(d1, -e);
-      d2 = scalbnf(d2, -e);
-      d3 = scalbnf(d3, -e);
+      // -d gives the same band (F_minus and F_plus exchange and change sign)
+      const float sg = d3 < 0.f ? -1.f : 1.f;
+      d1 = sg * scalbnf(d1, -e);
+      d2 = sg * scalbnf(d2, -e);
+      d3 = sg * scalbnf(d3, -e);
       const float ed = eps * sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
       const float Cm = d3 - ed, Cp = d3 + ed;
       const float iCm = Cm != 0.f ? __frcp_rn(Cm) : 0.f, iCp = Cp != 0.f ? __frcp_rn(Cp) : 0.f;
-      for (int r = R0 + lane; r < R1; r += 32) {
+      if (Cm > 1e-20f) {
+        // Cm > 0 (below 1e-20 the general rows below: a disc far beyond the grid's reach of
+        // float32). {F_minus < 0} is the disc of centre -(d1, d2)/Cm and radius sqrt(d1^2 + d2^2 + Cm Cp)/Cm:
+        // rows beyond its extent (with a margin for the float32 error of the bounds) have
+        // min F_minus > 0 well outside the decision band
+        const float vc = -d2 * iCm, rad = sqrtf(fmaf(d1, d1, fmaf(d2, d2, Cm * Cp))) * iCm;
+        const float mg = 2.f + 1e-5f * (fabsf(vc) + rad) * half;
+        const float flo = fmaf(vc - rad, half, half) - mg, fhi = fmaf(vc + rad, half, half) + mg;
+        const int r_lo = max(R0, (int)floorf(fminf(fmaxf(flo, -1.f), (float)G)));
+        const int r_hi = min(R1 - 1, (int)fminf(fmaxf(fhi, -1.f), (float)G));
+        // S1 is one interval (the disc's chord) or empty, S2 the outside of one interval or
+        // everything, so a row votes at most two runs. A discriminant at most 1e-30 leaves a
+        // sliver of S1 (no cell) or of S2's complement (no cell inside it) whose cells have |F|
+        // below 1e-10: inside the decision band.
+        //
+        // The v parts Cm v^2 + 2 d2 v and Cp v^2 + 2 d2 v are convex: the maximum of the second
+        // over a strip is at one of its lines, and so is the minimum of the first except in the
+        // strip holding its vertex vc, where it is -d2^2/Cm. (A vertex within rounding of a line
+        // gives the two strips beside it minima that differ by a square of that rounding.)
+        const int rv = __float2int_rd(fmaf(vc, half, half));
+        const float hvert = -d2 * d2 * iCm, d2x2 = d2 + d2;
+        for (int r = r_lo + lane; r <= r_hi; r += 32) {
+          const float v0 = fmaf((float)r, step, -1.f), v1 = v0 + step;
+          float hm = fminf(v0 * fmaf(Cm, v0, d2x2), v1 * fmaf(Cm, v1, d2x2));
+          if (r == rv) hm = fminf(hm, hvert);
+          const float mr = hm - Cp;
+          const float discA = fmaf(-Cm, mr, d1 * d1);
+          if (!(discA > 1e-30f)) continue;
+          float r1, r2;
+          roots2_apx(iCm, d1, mr, discA, r1, r2);
+          // cells meeting (r1, r2): columns floor((r1 + 1) G/2) .. ceil((r2 + 1) G/2) - 1, the
+          // saturated conversions clamped to [0, G] before the subtraction
+          const int a0 = clampi(__float2int_rd(fmaf(r1, half, half)), G);
+          const int a1 = clampi(__float2int_ru(fmaf(r2, half, half)), G) - 1;
+          const float Mr = fmaxf(v0 * fmaf(Cp, v0, d2x2), v1 * fmaf(Cp, v1, d2x2)) - Cm;
+          const float discB = fmaf(-Cp, Mr, d1 * d1);
+          int x1 = G - 1, x2 = G;  // S2's columns: [0, x1] and [x2, G - 1]
+          if (discB > 1e-30f) {
+            float s1, s2;
+            roots2_apx(iCp, d1, Mr, discB, s1, s2);
+            x1 = clampi(__float2int_ru(fmaf(s1, half, half)), G) - 1;
+            x2 = clampi(__float2int_rd(fmaf(s2, half, half)), G);
+          }
+          const uint32_t rowbase = sbase + 4u * (uint32_t)(((r - R0) >> 1) * G);
+          const uint32_t inc = ((r - R0) & 1) ? 0x10000u : 1u;
+          if (x2 <= x1 + 1) {
+            vote_run(rowbase, inc, G, a0, a1);
+          } else {
+            vote_run(rowbase, inc, G, a0, min(a1, x1));
+            vote_run(rowbase, inc, G, max(a0, x2), a1);
+          }
+        }
+        continue;
+      }
+      for (int r = R0 + lane; r < R1; r += 32) {  // Cm <= 0 (about 0.2% of the headline's circles)
         const float v0 = fmaf((float)r, step, -1.f), v1 = fmaf((float)(r + 1), step, -1.f);
         // F_minus = Cm (u^2 + v^2) + 2 d1 u + 2 d2 v - Cp ; F_plus = Cp (u^2 + v^2) + 2 d1 u + 2 d2 v - Cm
         const float mr = quad_extreme(Cm, iCm, d2, v0, v1, true) - Cp;
         const float Mr = quad_extreme(Cp, iCp, d2, v0, v1, false) - Cm;
         const Ranges A = cell_ranges(Cm, iCm, d1, mr, 1.f, half, G);   // Cm u^2 + 2 d1 u + mr < 0
         const Ranges B = cell_ranges(Cp, iCp, d1, Mr, -1.f, half, G);  // Cp u^2 + 2 d1 u + Mr > 0
+        const uint32_t rowbase = sbase + 4u * (uint32_t)(((r - R0) >> 1) * G);
+        const uint32_t inc = ((r - R0) & 1) ? 0x10000u : 1u;
         for (int x = 0; x < A.n; ++x)
-          for (int y = 0; y < B.n; ++y)
-            vote_span(sbase, W, r - R0, max(A.a[x], B.a[y]), min(A.b[x], B.b[y]));
+          for (int y = 0; y < B.n; ++y) vote_run(rowbase, inc, G, max(A.a[x], B.a[y]), min(A.b[x], B.b[y]));
       }
     }
     __syncthreads();
-    uint4* out = reinterpret_cast<uint4*>(D.partial + ((int64_t)I.slice * G + R0) * W);
-    for (int g = threadIdx.x; g < (words >> 2); g += blockDim.x) out[g] = t4[g];
+    flush_row_pair_tile(tile, G, R0, R1, D.partial + (int64_t)I.slice * G * (G >> 1));
     __syncthreads();
   }
 }

@@ -46,6 +46,7 @@
 // float32 roundings of zero: inside the band in which the closed-cell test may go either way.
 #include <stdint.h>
 
+#include "row_tiles.cuh"
 #include "sprot_internal.h"
 
 namespace sprot {
@@ -535,35 +536,9 @@ __device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, u
   }
   __syncthreads();
 
-  uint4* out4 = reinterpret_cast<uint4*>(D.partial + (int64_t)I.slice * G * W2);
+  uint32_t* out = D.partial + (int64_t)I.slice * G * W2;
   if (ROWS) {
-    // prefix sums along each row pair (a warp per row pair), then each row's counters in
-    // column pairs
-    for (int rp = warp; rp < ((B.R1 - B.R0) >> 1); rp += kRunWarps) {
-      uint32_t* row = tile + rp * G;
-      uint32_t carry = 0;
-      for (int c0 = 0; c0 < G; c0 += 32) {
-        const int c = c0 + lane;
-        uint32_t v = c < G ? row[c] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(kFull, v, o);
-          if (lane >= o) v += t;
-        }
-        v += carry;
-        if (c < G) row[c] = v;
-        carry = __shfl_sync(kFull, v, 31);
-      }
-    }
-    __syncthreads();
-    for (int g = threadIdx.x; g < (((B.R1 - B.R0) * W2) >> 2); g += blockDim.x) {
-      const int rr = (4 * g) / W2, c2 = 4 * g - rr * W2;
-      const uint4* rw = reinterpret_cast<const uint4*>(tile + (rr >> 1) * G + 2 * c2);
-      const uint4 ra = rw[0], rb = rw[1];
-      const int sh = (rr & 1) ? 16 : 0;
-      auto pk = [sh](uint32_t x, uint32_t y) { return ((x >> sh) & 0xffffu) | (((y >> sh) & 0xffffu) << 16); };
-      out4[((B.R0 + rr) * W2 + c2) >> 2] = make_uint4(pk(ra.x, ra.y), pk(ra.z, ra.w), pk(rb.x, rb.y), pk(rb.z, rb.w));
-    }
+    flush_row_pair_tile(tile, G, B.R0, B.R1, out);
   } else {
     // prefix sums down each word column in chunks of rows (a thread per column and chunk), the
     // chunks' carries, then the rows
@@ -592,7 +567,7 @@ __device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, u
       const int rr = (4 * g) / W, c2 = 4 * g - rr * W;
       const uint4 v = reinterpret_cast<const uint4*>(tile)[g];
       const uint4 c = *reinterpret_cast<const uint4*>(carry + (rr / rpc) * W + c2);
-      out4[(rr * W2 + (B.C0 >> 1) + c2) >> 2] = make_uint4(v.x + c.x, v.y + c.y, v.z + c.z, v.w + c.w);
+      reinterpret_cast<uint4*>(out)[(rr * W2 + (B.C0 >> 1) + c2) >> 2] = make_uint4(v.x + c.x, v.y + c.y, v.z + c.z, v.w + c.w);
     }
   }
   __syncthreads();
