@@ -597,8 +597,10 @@ def run_eps(B, P, Q, G, reps=5):
     return out
 
 
-def run_batched(B, dev, m=4096, loop_sample=512):
-    """4096 uneven instances in one batched solve vs a per-instance loop of single solves."""
+def run_batched(B, dev, m=4096):
+    """4096 uneven instances in one batched solve, with the default plan and with the plan the
+    autotuner picks for the batch's class, against a per-instance loop of single solves over all
+    4096 instances."""
     import torch
 
     from paper_2502_06337_gb300 import synth
@@ -613,41 +615,63 @@ def run_batched(B, dev, m=4096, loop_sample=512):
         probs.append((P, Q, B.make_params(grid=0, angle_bins=360, tau=tau), pb))
         total += s["n"]
     batch = [(P, Q, prm) for P, Q, prm, _ in probs]
-    B.estimate_batch(batch)  # warm-up (allocates the workspace)
-    torch.cuda.synchronize()
     reps = 3
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        res, grids = B.estimate_batch(batch)
-    t_batch = (time.perf_counter() - t0) / reps
-    # per-instance loop of the plain single solve on the first loop_sample instances (same params)
-    sub = probs[:loop_sample]
-    for P, Q, prm, _ in sub[:8]:
+
+    def time_batch():
+        B.estimate_batch(batch)  # warm-up (workspace, graph capture)
+        B.estimate_batch(batch)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            res, grids = B.estimate_batch(batch)
+        return (time.perf_counter() - t0) / reps, res, grids
+
+    B.autotune_reset()
+    t_batch, res, grids = time_batch()
+    knobs = B.autotune_batch(batch, reps=2)
+    t_tuned, res_t, _ = time_batch()
+    B.autotune_reset()
+    # per-instance loop of the plain single solve on every instance (same params and G)
+    for P, Q, prm, _ in probs[:8]:
         B.estimate_rotations(P, Q, B.make_params(grid=grids[0], angle_bins=360, tau=prm.tau), allow_noaxis=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     loop_res = []
-    for i, (P, Q, prm, _) in enumerate(sub):
+    for i, (P, Q, prm, _) in enumerate(probs):
         p1 = B.make_params(grid=grids[i], angle_bins=360, tau=prm.tau)
         loop_res.append(B.estimate_rotations(P, Q, p1, allow_noaxis=True))
-    t_loop = (time.perf_counter() - t0) * (m / len(sub))
+    t_loop = time.perf_counter() - t0
     # integer results identical; FP64 rotations equal up to summation order (max |dR|; the
     # arccos of Eq. 16 cannot resolve differences this small)
-    same = all(len(a) == len(b) and all(x["cell"] == y["cell"] and x["bin"] == y["bin"] and
-                                         x["n_inliers"] == y["n_inliers"] and
-                                         float(np.max(np.abs(x["R"] - y["R"]))) < 1e-9 for x, y in zip(a, b))
-               for a, b in zip(res[:len(sub)], loop_res))
+
+    def same(ra, rb):
+        return all(len(a) == len(b) and all(x["cell"] == y["cell"] and x["bin"] == y["bin"] and
+                                            x["n_inliers"] == y["n_inliers"] and
+                                            float(np.max(np.abs(x["R"] - y["R"]))) < 1e-9 for x, y in zip(a, b))
+                   for a, b in zip(ra, rb))
+
     errs = [math.degrees(_rot_err(pb.rotations[0], r[0]["R"])) for (_, _, _, pb), r in zip(probs, res) if r]
     return {"instances": m, "correspondences": total, "batch_s": t_batch,
             "solves_per_s": m / t_batch, "Mcorr_per_s": total / t_batch / 1e6,
+            "tuned": {"knobs": {k: knobs[k] for k in ("batch_slice", "batch_div")},
+                      "solves_per_s": m / t_tuned, "batch_s": t_tuned,
+                      "tuner_ms_default": knobs["ms_default"], "tuner_ms_tuned": knobs["ms_tuned"],
+                      "same_results_as_untuned": bool(same(res_t, res))},
             "loop_solves_per_s": m / t_loop, "speedup_vs_loop": t_loop / t_batch,
-            "loop_extrapolated_from": len(sub), "same_results_as_loop": bool(same),
+            "loop_instances": m, "same_results_as_loop": bool(same(res, loop_res)),
             "median_rot_err_deg": float(np.median(errs)) if errs else None,
             "frac_rot_err_below_1deg": float(np.mean(np.array(errs) < 1.0)) if errs else None}
 
 
-def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40):
-    """Poisson arrivals into the continuous-batching server; latency from submit to done."""
+def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40, saturated_requests=3000,
+               in_flight=256):
+    """The continuous-batching server on the served mix (n log-uniform in [1e3, 1e6], 1-3
+    rotations; host inputs): (1) Poisson arrivals at rate_hz, latency from submit to done;
+    (2) at capacity: a closed loop keeping in_flight requests submitted, its throughput and
+    latency; (3) the same request sequence as a loop of plain single solves from host
+    inputs (sprot_estimate_rotations_k with HOST_PTRS, one call after another)."""
+    from collections import deque
+
     from paper_2502_06337_gb300 import synth
 
     m = int(duration_s * rate_hz)
@@ -659,6 +683,8 @@ def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40):
         pb = synth.make_problem(s["n"], s["inlier_fracs"], s["sigma"], seed=s["seed"])
         k = len(s["inlier_fracs"])
         probs.append((pb, B.make_params(grid=0, angle_bins=360, k=k, nms_deg=2.0, tau=synth.default_tau(0.01))))
+    rng = np.random.default_rng(3)
+    seq = [int(j) for j in rng.integers(0, pool, size=saturated_requests)]
     srv = B.Server(budget_gb << 30, max_batch=256)
     try:
         # warm-up: every pool problem once, all in flight (sizes the workers' arenas and
@@ -675,18 +701,72 @@ def run_served(B, duration_s=3.0, rate_hz=2000.0, pool=48, budget_gb=40):
             tickets.append((srv.submit(pb.P, pb.Q, prm), i % pool))
         results = [(srv.wait(t), j) for t, j in tickets]
         wall = time.perf_counter() - t0
+        # closed loop at capacity
+        sat = []
+        q = deque()
+        t1 = time.perf_counter()
+        for j in seq:
+            if len(q) >= in_flight:
+                sat.append(srv.wait(q.popleft()))
+            pb, prm = probs[j]
+            q.append(srv.submit(pb.P, pb.Q, prm))
+        while q:
+            sat.append(srv.wait(q.popleft()))
+        sat_wall = time.perf_counter() - t1
     finally:
         srv.close()
+    # the same sequence as a loop of plain solves from host inputs
+    host = []
+    for pb, prm in probs:
+        p1 = B.make_params(grid=prm.grid, angle_bins=prm.angle_bins, k=prm.k, nms_deg=prm.nms_deg,
+                           tau=prm.tau, flags=B.HOST_PTRS)
+        host.append((pb.P, pb.Q, p1))
+    for P, Q, p1 in host[:8]:
+        B.estimate_rotations(P, Q, p1, allow_noaxis=True)
+    t2 = time.perf_counter()
+    loop = [B.estimate_rotations(*host[j], allow_noaxis=True) for j in seq]
+    loop_wall = time.perf_counter() - t2
+    # the GPU-bound ceiling: the same sequence from device-resident inputs, solved as batches of
+    # in_flight requests with no host copies
+    import torch
+
+    dev_probs = [(torch.from_numpy(pb.P).cuda(), torch.from_numpy(pb.Q).cuda(), prm) for pb, prm in probs]
+    chunks = [[dev_probs[j] for j in seq[a:a + in_flight]] for a in range(0, len(seq), in_flight)]
+    B.estimate_batch(chunks[0])
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    for c in chunks:
+        B.estimate_batch(c)
+    ceiling_wall = time.perf_counter() - t3
+    del dev_probs, chunks
+    same = all(len(r["rotations"]) == len(lr) and
+               all(tuple(a["cell"]) == tuple(b["cell"]) and a["bin"] == b["bin"] and a["n_inliers"] == b["n_inliers"]
+                   for a, b in zip(r["rotations"], lr))
+               for r, lr in zip(sat, loop))
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r, _ in results])
     first = min(r["t_submit_ms"] for r, _ in results)
     last = max(r["t_done_ms"] for r, _ in results)
     ok = sum(1 for r, _ in results if r["status"] == 0)
     corr = sum(probs[j][0].n for _, j in results)
+    sat_lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in sat])
+    sat_corr = sum(probs[j][0].n for j in seq)
     return {"requests": m, "completed_ok": ok, "offered_rate_hz": rate_hz,
             "solves_per_s": m / ((last - first) / 1e3), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_n": corr / m,
             "Mcorr_per_s": corr / ((last - first) / 1e3) / 1e6, "wall_s": wall,
-            "budget_gb": budget_gb, "pool_problems": pool}
+            "budget_gb": budget_gb, "pool_problems": pool,
+            "saturated_requests": len(seq), "saturated_in_flight": in_flight,
+            "saturated_solves_per_s": len(seq) / sat_wall,
+            "saturated_ok": sum(1 for r in sat if r["status"] == 0),
+            "saturated_p50_ms": float(np.percentile(sat_lat, 50)),
+            "saturated_p99_ms": float(np.percentile(sat_lat, 99)),
+            "saturated_Mcorr_per_s": sat_corr / sat_wall / 1e6,
+            "loop_solves_per_s": len(seq) / loop_wall,
+            "saturated_vs_loop": loop_wall / sat_wall,
+            "device_batches_solves_per_s": len(seq) / ceiling_wall,
+            "loop_same_results": bool(same),
+            "note": "host inputs (pageable numpy) on every path; the loop calls "
+                    "sprot_estimate_rotations_k with HOST_PTRS once per request"}
 
 
 def main():

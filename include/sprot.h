@@ -272,6 +272,62 @@ int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream);
 /* Accumulator side the autotuner picks for n pairs (used when params.grid == 0). */
 int32_t sprot_autotune_grid(int64_t n);
 
+/* ---- plan autotuning ---------------------------------------------------------------------
+ * The grid side G above is chosen for accuracy (Sec. IV-A: the accumulator's resolution).
+ * The knobs below change only how the work is cut, never a result's integer parts: the
+ * accumulator is an exact count whatever the slicing, and the FP64 sums differ only in their
+ * summation order (results within 1e-9 of the default plan's). The paper has no counterpart;
+ * it is this library's speed tuning.
+ *
+ * sprot_autotune_plan / sprot_autotune_batch time a small candidate set of knobs on the
+ * caller's own inputs on the current device and store the fastest for the input's class in a
+ * process-wide table; every later solve of that class on that device (sprot_estimate_*,
+ * sprot_estimate_batch and the server's batches) then uses it. Classes: one problem, by
+ * (device, bit length of n, G); a batch of m instances, by (device, bit length of the mean n). */
+typedef struct sprot_plan_knobs {
+  int32_t vote_rounds; /* one problem: the vote's (slice x band) items fill this many rounds of
+                          the SMs, 1-3 (more slices than the 16-bit counters need balance
+                          uneven items; each slice costs a partial accumulator) (default 1) */
+  int32_t chunk_div;   /* one problem: the per-pair passes cut the n pairs into about this many
+                          items, 100-2400 (default 600) */
+  int32_t batch_slice; /* batch: circles per vote slice of an instance, 16384-65535 (32768) */
+  int32_t batch_div;   /* batch: the per-pair passes cut the batch's pairs into about this many
+                          items, 300-4800 (default 1200) */
+  double ms_tuned;     /* set by the tuner: median solve time of the winner (ms, wall clock) */
+  double ms_default;   /* set by the tuner: median solve time of the default knobs (ms) */
+} sprot_plan_knobs;
+
+/* The default (untuned) knobs; ms fields 0. */
+void sprot_default_knobs(sprot_plan_knobs* k);
+
+/* Times the single solve of (P, Q, n, params) -- the arguments of sprot_estimate_rotations_k,
+ * HOST_PTRS allowed -- under each candidate (vote_rounds 1-3 x chunk_div 300/600/1200: two
+ * untimed runs, then the median of `reps` timed runs, reps 1-15) and stores the fastest for
+ * the class of (n, G) on the current device (G: params->grid, or sprot_autotune_grid(n)).
+ * *out receives the winner with both times. Errors: E_INVAL (bad arguments), E_NOMEM,
+ * E_CUDA; E_NOAXIS from a solve does not stop the tuning. */
+int sprot_autotune_plan(const float* P, const float* Q, int64_t n, const sprot_params* params,
+                        int32_t reps, sprot_plan_knobs* out, void* stream);
+
+/* As sprot_autotune_plan for a batch (the arguments of sprot_estimate_batch; candidates
+ * batch_slice 16384/32768/65535 x batch_div 600/1200/2400), stored for the class of the
+ * batch's mean n. The instances' outputs hold the last timed run's results (the winner's
+ * plan, equal to any other plan's up to FP64 summation order). */
+int sprot_autotune_batch(sprot_instance* inst, int64_t m, int32_t reps, sprot_plan_knobs* out, void* stream);
+
+/* The knobs a solve on the current device would use: for one problem of n pairs on G x G
+ * (batched = 0), or for a batch whose mean instance has n pairs (batched = 1, G ignored).
+ * Returns 1 and the stored knobs when that class was tuned, else 0 and the defaults. */
+int32_t sprot_tuned_plan(int64_t n, int32_t grid_size, int32_t batched, sprot_plan_knobs* out);
+
+/* Stores knobs for a class on the current device, as a tuner would (for example knobs saved
+ * from an earlier process's tuning). Errors: E_INVAL when a knob is outside its range above,
+ * E_CUDA when there is no current device. */
+int sprot_set_tuned_plan(int64_t n, int32_t grid_size, int32_t batched, const sprot_plan_knobs* k);
+
+/* Forgets every tuned class (later solves use the defaults). */
+void sprot_autotune_reset(void);
+
 /* ---- serving ------------------------------------------------------------------------------ */
 
 typedef struct sprot_server sprot_server;

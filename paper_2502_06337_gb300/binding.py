@@ -29,6 +29,8 @@ EXPORTS = [
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
     "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan", "sprot_axis_vote_noalloc",
+    "sprot_default_knobs", "sprot_autotune_plan", "sprot_autotune_batch", "sprot_tuned_plan",
+    "sprot_set_tuned_plan", "sprot_autotune_reset",
 ]
 
 
@@ -65,6 +67,14 @@ class Instance(C.Structure):
     _fields_ = [("P", C.c_void_p), ("Q", C.c_void_p), ("n", C.c_int64), ("params", Params),
                 ("out", C.POINTER(Rotation)), ("n_found", C.POINTER(C.c_int32)),
                 ("labels", C.c_void_p)]
+
+
+class Knobs(C.Structure):
+    _fields_ = [("vote_rounds", C.c_int32), ("chunk_div", C.c_int32), ("batch_slice", C.c_int32),
+                ("batch_div", C.c_int32), ("ms_tuned", C.c_double), ("ms_default", C.c_double)]
+
+    def to_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class ServerCfg(C.Structure):
@@ -119,6 +129,15 @@ def load(path: str = LIB_PATH):
     lib.sprot_estimate_batch.argtypes = [C.POINTER(Instance), i64, vp]
     lib.sprot_autotune_grid.argtypes = [i64]
     lib.sprot_autotune_grid.restype = i32
+    lib.sprot_default_knobs.argtypes = [C.POINTER(Knobs)]
+    lib.sprot_default_knobs.restype = None
+    lib.sprot_autotune_plan.argtypes = [vp, vp, i64, C.POINTER(Params), i32, C.POINTER(Knobs), vp]
+    lib.sprot_autotune_batch.argtypes = [C.POINTER(Instance), i64, i32, C.POINTER(Knobs), vp]
+    lib.sprot_tuned_plan.argtypes = [i64, i32, i32, C.POINTER(Knobs)]
+    lib.sprot_tuned_plan.restype = i32
+    lib.sprot_set_tuned_plan.argtypes = [i64, i32, i32, C.POINTER(Knobs)]
+    lib.sprot_autotune_reset.argtypes = []
+    lib.sprot_autotune_reset.restype = None
     lib.sprot_server_create.argtypes = [C.POINTER(ServerCfg), C.POINTER(vp)]
     lib.sprot_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
     lib.sprot_server_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(Result)]
@@ -137,7 +156,7 @@ def load(path: str = LIB_PATH):
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
                  "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_axis_vote_noalloc", "sprot_axis_vote_eps", "sprot_refine_axis",
                  "sprot_select_peaks",
-                 "sprot_estimate_batch",
+                 "sprot_estimate_batch", "sprot_autotune_plan", "sprot_autotune_batch", "sprot_set_tuned_plan",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
                  "sprot_server_destroy", "sprot_probe_smem_atomic_rate"]:
         getattr(lib, name).restype = C.c_int
@@ -346,12 +365,11 @@ class BatchResult:
         return (self._one(i) for i in range(len(self)))
 
 
-def estimate_batch(problems, stream=None):
-    """problems: list of (P, Q, Params[, labels]) with device tensors. Returns (BatchResult,
-    array of the grid sides used). The instance table is built as one numpy record array in
-    the layout of sprot_instance, so that a batch of thousands costs no per-field Python work."""
+def _instance_table(problems):
+    """The sprot_instance table of a batch as one numpy record array in the layout of
+    sprot_instance (a batch of thousands costs no per-field Python work), with the output
+    arrays it points into: (table, rotations, n_found, kmax)."""
     global _INSTANCE_FIELDS
-    lib = load()
     if _INSTANCE_FIELDS is None:
         _INSTANCE_FIELDS = _struct_dtype(Instance)
     m = len(problems)
@@ -384,9 +402,63 @@ def estimate_batch(problems, stream=None):
         tab["params." + name] = col
     tab["out"] = rot.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(kmax * C.sizeof(Rotation))
     tab["n_found"] = n_found.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(4)
-    st = lib.sprot_estimate_batch(tab.ctypes.data_as(C.POINTER(Instance)), m, _stream(stream))
+    return tab, rot, n_found, kmax
+
+
+def estimate_batch(problems, stream=None):
+    """problems: list of (P, Q, Params[, labels]) with device tensors. Returns (BatchResult,
+    array of the grid sides used)."""
+    tab, rot, n_found, kmax = _instance_table(problems)
+    st = load().sprot_estimate_batch(tab.ctypes.data_as(C.POINTER(Instance)), len(problems), _stream(stream))
     check(st, "sprot_estimate_batch")
     return BatchResult(rot, n_found, kmax), tab["params.grid"].copy()
+
+
+def default_knobs() -> dict:
+    k = Knobs()
+    load().sprot_default_knobs(C.byref(k))
+    return k.to_dict()
+
+
+def autotune_plan(P, Q, params: Params, reps: int = 3, stream=None) -> dict:
+    """Times the candidate plans of the single solve of (P, Q, params) and stores the fastest
+    for its class (sprot_autotune_plan). Returns the winner's knobs with both times."""
+    _check_points(P, Q)
+    k = Knobs()
+    st = load().sprot_autotune_plan(_ptr(P), _ptr(Q), P.shape[0], C.byref(params), int(reps), C.byref(k),
+                                    _stream(stream))
+    check(st, "sprot_autotune_plan")
+    return k.to_dict()
+
+
+def autotune_batch(problems, reps: int = 3, stream=None) -> dict:
+    """As autotune_plan for a batch (sprot_autotune_batch); problems as for estimate_batch."""
+    # the table points into rot and n_found: they must outlive the call
+    tab, rot, n_found, _ = _instance_table(problems)
+    k = Knobs()
+    st = load().sprot_autotune_batch(tab.ctypes.data_as(C.POINTER(Instance)), len(problems), int(reps),
+                                     C.byref(k), _stream(stream))
+    del rot, n_found
+    check(st, "sprot_autotune_batch")
+    return k.to_dict()
+
+
+def tuned_plan(n: int, G: int = 0, batched: bool = False):
+    """(tuned?, knobs) a solve of this class would use on the current device."""
+    k = Knobs()
+    found = load().sprot_tuned_plan(int(n), int(G), 1 if batched else 0, C.byref(k))
+    return bool(found), k.to_dict()
+
+
+def set_tuned_plan(n: int, knobs: dict, G: int = 0, batched: bool = False):
+    """Stores knobs for the class of (n, G) or of a batch with mean n (sprot_set_tuned_plan)."""
+    k = Knobs(*[int(knobs[f]) if f not in ("ms_tuned", "ms_default") else float(knobs.get(f, 0.0))
+                for f, _ in Knobs._fields_])
+    check(load().sprot_set_tuned_plan(int(n), int(G), 1 if batched else 0, C.byref(k)), "sprot_set_tuned_plan")
+
+
+def autotune_reset():
+    load().sprot_autotune_reset()
 
 
 class Server:

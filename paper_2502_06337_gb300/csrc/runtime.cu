@@ -7,7 +7,9 @@
 // instance table, copied to the device in one transfer; the kernels then run on the caller's
 // stream in a fixed order with no host round trip until the final results copy.
 #include <algorithm>
+#include <array>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -307,26 +309,31 @@ std::shared_ptr<Workspace> workspace_for(cudaStream_t st, int* status) {
 }
 
 
-// Pairs per work item of the per-pair kernels. One problem: about 600 items, so that the
-// problem alone fills the GPU. A batch: sized from the batch's total (the instances provide the
-// parallelism), so that small instances do not pay a block's fixed cost per few hundred pairs.
-int stream_chunk(int64_t n) {
-  int64_t c = (n + 599) / 600;
+// The plan's knobs (the autotuner's search space); the defaults are the untuned plan.
+sprot_plan_knobs default_knobs() { return sprot_plan_knobs{1, 600, 32768, 1200, 0.0, 0.0}; }
+
+// Pairs per work item of the per-pair kernels. One problem: about `div` items (600 by
+// default), so that the problem alone fills the GPU. A batch: sized from the batch's total (the
+// instances provide the parallelism), so that small instances do not pay a block's fixed cost
+// per few hundred pairs. At least 256 pairs an item.
+int stream_chunk(int64_t n, int div = 600) {
+  int64_t c = (n + div - 1) / div;
   c = (c + 255) / 256 * 256;
   return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
 }
 
-int batch_chunk(int64_t total) {
-  int64_t c = (total + 1199) / 1200;
+int batch_chunk(int64_t total, int div = 1200) {
+  int64_t c = (total + div - 1) / div;
   c = (c + 255) / 256 * 256;
   return (int)std::min<int64_t>(std::max<int64_t>(c, 256), kStreamChunk);
 }
 
 // Vote layout of one instance: row bands that fit the shared tile, and circle slices (at most
 // 65535 circles each, so the 16-bit counters cannot overflow). A single problem is spread
-// over every SM; in a batch each instance gets slices of 32768 circles.
+// over every SM, its items filling `rounds` rounds of the SMs; in a batch each instance gets
+// slices of batch_slice circles.
 void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false,
-               int64_t max_slices = INT64_MAX) {
+               int64_t max_slices = INT64_MAX, int rounds = 1, int batch_slice = 32768) {
   if (eps)
     plan_bands(ip.G, kMaxSmemBytes, eps_row_bytes(ip.G), 0, &ip.T, ip.row0);
   else
@@ -334,17 +341,40 @@ void plan_vote(InstPlan& ip, int64_t n, bool single, int nsm, bool eps = false,
   const int64_t s_min = (n + kMaxSliceCircles - 1) / kMaxSliceCircles;
   // the curve vote has 2 T items per slice (row bands and column bands), the eps-band vote T
   const int per_slice = (eps ? 1 : 2) * std::max(ip.T, 1);
-  int64_t s = single ? std::max<int64_t>(1, nsm / per_slice) : (n + 32767) / 32768;
-  if (single && s < s_min) {
-    // the counters force more slices than one round of the SMs holds: the most slices whose
-    // items fill whole rounds (k rounds, k * nsm >= s_min * per_slice), so that no round runs
-    // with most SMs idle
-    const int64_t k = (s_min * per_slice + nsm - 1) / nsm;
-    s = k * nsm / per_slice;
+  int64_t s;
+  if (single) {
+    // k rounds of the SMs, at least as many as the counters force (k nsm >= s_min per_slice),
+    // so that no round runs with most SMs idle: the most slices whose items fit them
+    const int64_t k = std::max<int64_t>(rounds, (s_min * per_slice + nsm - 1) / nsm);
+    s = std::max<int64_t>(1, k * nsm / per_slice);
+  } else {
+    s = (n + batch_slice - 1) / batch_slice;
   }
   s = std::min<int64_t>(s, std::max<int64_t>(1, (n + 511) / 512));
   s = std::min<int64_t>(s, max_slices);
   ip.S = (int)std::max(s, s_min);
+}
+
+// Tuned knobs, per class: {device, 0, bit length of n, G} for one problem, {device, 1, bit
+// length of the mean n, 0} for a batch.
+using TuneKey = std::array<int64_t, 4>;
+std::mutex g_tune_mu;
+std::map<TuneKey, sprot_plan_knobs> g_tuned;
+
+int bit_length(int64_t x) {
+  int b = 0;
+  for (; x > 0; x >>= 1) ++b;
+  return b;
+}
+TuneKey tune_key(int dev, bool batched, int64_t n, int G) {
+  return TuneKey{dev, batched ? 1 : 0, bit_length(n), batched ? 0 : G};
+}
+bool tuned_lookup(const TuneKey& key, sprot_plan_knobs* kn) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tuned.find(key);
+  if (it == g_tuned.end()) return false;
+  *kn = it->second;
+  return true;
 }
 
 int tile_bytes(const InstPlan& ip, bool eps = false) {
@@ -387,8 +417,15 @@ void release_workspace(cudaStream_t st) {
 }
 
 size_t problem_footprint(int64_t n, int G, int J, int k) {
-  int64_t S = std::max<int64_t>((n + 32767) / 32768, (n + kMaxSliceCircles - 1) / kMaxSliceCircles);
-  int64_t items = (n + stream_chunk(n) - 1) / stream_chunk(n);
+  // the most slices any plan within the knobs' ranges gives the problem: alone (three rounds of
+  // the SMs) or in a batch (slices of 16384 circles); at most one per-pair item per 256 pairs
+  int dev = 0;
+  cudaGetDevice(&dev);
+  InstPlan ip{};
+  ip.G = G;
+  plan_vote(ip, n, true, sm_count(dev), false, INT64_MAX, 3);
+  const int64_t S = std::max<int64_t>(ip.S, (n + 16383) / 16384);
+  const int64_t items = (n + 255) / 256;
   return align_up((size_t)2 * S * G * (G / 2) * 4) + align_up((size_t)G * G * 4) +
          align_up((size_t)k * n * 2) + align_up((size_t)2 * items * k * 80) + align_up((size_t)n * 4) +
          align_up((size_t)k * J * 4) + align_up(sizeof(DevRot) * k) + 4096;
@@ -440,7 +477,7 @@ bool run_graph(Workspace* ws, const std::vector<uint64_t>& key, cudaStream_t st,
 }
 
 // Solves a batch of problems on stream st. Every Problem must be validated already.
-int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
+int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot_plan_knobs* force) {
   const int m = (int)probs.size();
   int status = SPROT_OK;
   std::shared_ptr<Workspace> ws = workspace_for(st, &status);
@@ -452,6 +489,13 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
   std::vector<InstPlan> plan(m);
   int64_t total_n = 0;
   for (int i = 0; i < m; ++i) total_n += probs[i].n;
+  sprot_plan_knobs kn = default_knobs();
+  if (force)
+    kn = *force;
+  else
+    tuned_lookup(tune_key(ws->device, m > 1, m > 1 ? total_n / m : probs[0].n,
+                          probs[0].prm.grid ? probs[0].prm.grid : sprot_autotune_grid(probs[0].n)),
+                 &kn);
   // slice-reduction items: 512 words (one 16-byte column per thread) for one problem; in a
   // batch about 64 x 512 word-slices per item (an item reads every slice of its words), between
   // 512 and 8192 words
@@ -471,7 +515,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     ip.window = pb.prm.angle_window;
     ip.tau = (float)pb.prm.tau;
     ip.cos_nms = std::cos((double)pb.prm.nms_deg * 3.14159265358979323846 / 180.0);
-    plan_vote(ip, pb.n, m == 1, nsm);
+    plan_vote(ip, pb.n, m == 1, nsm, false, INT64_MAX, kn.vote_rounds, kn.batch_slice);
     if (ip.T <= 0) return SPROT_E_INVAL;
     vote_tile = std::max(vote_tile, tile_bytes(ip));
     for (int sl = 0; sl < ip.S; ++sl) {
@@ -489,7 +533,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs) {
     for (int64_t w0 = 0; w0 < words; w0 += red_words)
       ritems.push_back(ReduceItem{i, 0, w0, std::min<int64_t>(w0 + red_words, words)});
     ip.n_ritems = (int)(ritems.size() - r0);
-    ip.chunk = m == 1 ? stream_chunk(pb.n) : batch_chunk(total_n);
+    ip.chunk = m == 1 ? stream_chunk(pb.n, kn.chunk_div) : batch_chunk(total_n, kn.batch_div);
     ip.item0 = (int)sitems.size();
     for (int64_t a = 0; a < pb.n; a += ip.chunk)
       sitems.push_back(StreamItem{i, 0, a, std::min<int64_t>(a + ip.chunk, pb.n)});
@@ -1025,6 +1069,155 @@ int sprot_estimate_batch(sprot_instance* inst, int64_t m, void* stream) {
   if (st == SPROT_OK)
     for (int64_t i = 0; i < m; ++i) inst[i].params.grid = pb[i].prm.grid;
   return st;
+}
+
+namespace sprot {
+namespace {
+
+// Median wall time (ms) of `reps` solves of probs under knobs kn, after two untimed runs (the
+// second captures the launch graph that the timed runs replay). status: the first failure
+// other than E_NOAXIS.
+double time_plan(std::vector<Problem>& probs, cudaStream_t st, const sprot_plan_knobs& kn, int reps,
+                 int* status) {
+  auto run = [&]() {
+    const int r = solve(probs, st, true, &kn);
+    if (r != SPROT_OK && r != SPROT_E_NOAXIS && *status == SPROT_OK) *status = r;
+  };
+  run();
+  run();
+  std::vector<double> t;
+  for (int r = 0; r < reps && *status == SPROT_OK; ++r) {
+    const auto t0 = std::chrono::steady_clock::now();
+    run();
+    t.push_back(std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
+  if (t.empty()) return 0.0;
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+// Times every candidate (the defaults first), stores the fastest under key and returns it.
+int tune(std::vector<Problem>& probs, cudaStream_t st, const std::vector<sprot_plan_knobs>& cands, int reps,
+         const TuneKey& key, sprot_plan_knobs* out) {
+  int status = SPROT_OK;
+  sprot_plan_knobs best = cands[0];
+  double best_ms = 0.0, default_ms = 0.0;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    const double ms = time_plan(probs, st, cands[c], reps, &status);
+    if (status != SPROT_OK) return status;
+    if (c == 0) default_ms = ms;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = cands[c];
+    }
+  }
+  // the outputs end with the winner's results
+  time_plan(probs, st, best, 1, &status);
+  if (status != SPROT_OK) return status;
+  best.ms_tuned = best_ms;
+  best.ms_default = default_ms;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  if (out) *out = best;
+  return SPROT_OK;
+}
+
+}  // namespace
+}  // namespace sprot
+
+void sprot_default_knobs(sprot_plan_knobs* k) {
+  if (k) *k = default_knobs();
+}
+
+int sprot_autotune_plan(const float* P, const float* Q, int64_t n, const sprot_params* params, int32_t reps,
+                        sprot_plan_knobs* out, void* stream) {
+  if (!params || reps < 1 || reps > 15) return SPROT_E_INVAL;
+  int st = validate(P, Q, n, params, params->k);
+  if (st != SPROT_OK) return st;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPROT_E_CUDA;
+  std::vector<sprot_rotation> rot(std::max(params->k, 1));
+  int32_t nf = 0;
+  std::vector<Problem> pb(1);
+  pb[0] = Problem{P, Q, n, *params, params->k, (params->flags & SPROT_HOST_PTRS) != 0, rot.data(), &nf,
+                  nullptr, nullptr, nullptr};
+  if (pb[0].prm.grid == 0) pb[0].prm.grid = sprot_autotune_grid(n);
+  std::vector<sprot_plan_knobs> cands;
+  cands.push_back(default_knobs());
+  for (int r = 1; r <= 3; ++r)
+    for (int d : {600, 300, 1200}) {
+      sprot_plan_knobs k = default_knobs();
+      k.vote_rounds = r;
+      k.chunk_div = d;
+      if (r != 1 || d != 600) cands.push_back(k);
+    }
+  return tune(pb, reinterpret_cast<cudaStream_t>(stream), cands, reps, tune_key(dev, false, n, pb[0].prm.grid), out);
+}
+
+int sprot_autotune_batch(sprot_instance* inst, int64_t m, int32_t reps, sprot_plan_knobs* out, void* stream) {
+  if (!inst || m < 2 || reps < 1 || reps > 15) return SPROT_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPROT_E_CUDA;
+  std::vector<Problem> pb((size_t)m);
+  int64_t total = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    const sprot_instance& x = inst[i];
+    int st = validate(x.P, x.Q, x.n, &x.params, x.params.k);
+    if (st != SPROT_OK || !x.out || (x.params.flags & SPROT_HOST_PTRS)) return SPROT_E_INVAL;
+    pb[i] = Problem{x.P, x.Q, x.n, x.params, x.params.k, false, x.out, x.n_found, x.labels, nullptr, nullptr};
+    if (pb[i].prm.grid == 0) pb[i].prm.grid = sprot_autotune_grid(x.n);
+    total += x.n;
+  }
+  std::vector<sprot_plan_knobs> cands;
+  cands.push_back(default_knobs());
+  for (int sl : {32768, 16384, 65535})
+    for (int d : {1200, 600, 2400}) {
+      sprot_plan_knobs k = default_knobs();
+      k.batch_slice = sl;
+      k.batch_div = d;
+      if (sl != 32768 || d != 1200) cands.push_back(k);
+    }
+  const int st = tune(pb, reinterpret_cast<cudaStream_t>(stream), cands, reps, tune_key(dev, true, total / m, 0), out);
+  if (st == SPROT_OK)
+    for (int64_t i = 0; i < m; ++i) inst[i].params.grid = pb[i].prm.grid;
+  return st;
+}
+
+int32_t sprot_tuned_plan(int64_t n, int32_t G, int32_t batched, sprot_plan_knobs* out) {
+  sprot_plan_knobs k = default_knobs();
+  int dev = 0;
+  bool found = false;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaGetLastError();
+    found = tuned_lookup(tune_key(dev, batched != 0, n, G ? G : sprot_autotune_grid(n)), &k);
+  } else {
+    cudaGetLastError();
+  }
+  if (out) *out = k;
+  return found ? 1 : 0;
+}
+
+int sprot_set_tuned_plan(int64_t n, int32_t G, int32_t batched, const sprot_plan_knobs* k) {
+  if (!k || n < 1 || !(k->vote_rounds >= 1 && k->vote_rounds <= 3 && k->chunk_div >= 100 && k->chunk_div <= 2400 &&
+                       k->batch_slice >= 16384 && k->batch_slice <= kMaxSliceCircles && k->batch_div >= 300 &&
+                       k->batch_div <= 4800))
+    return SPROT_E_INVAL;
+  if (!batched && G != 0 && (!is_pow2(G) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)) return SPROT_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SPROT_E_CUDA;
+  }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tuned[tune_key(dev, batched != 0, n, G ? G : sprot_autotune_grid(n))] = *k;
+  return SPROT_OK;
+}
+
+void sprot_autotune_reset(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tuned.clear();
 }
 
 void sprot_release_stream_workspace(void* stream) { release_workspace(reinterpret_cast<cudaStream_t>(stream)); }

@@ -104,8 +104,11 @@ struct Problem {
 
 // Solves the problems (validated by the caller) with one launch sequence on st and waits for
 // the results. Returns SPROT_OK, or for a single problem SPROT_E_NOAXIS when it has no peak.
-// graphs: replay the launch sequence from a CUDA graph when its shape repeats (see runtime.cu)
-int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true);
+// graphs: replay the launch sequence from a CUDA graph when its shape repeats (see runtime.cu).
+// force: plan knobs to use (the autotuner's trials); null: the tuned knobs of the call's class,
+// else the defaults.
+int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs = true,
+          const sprot_plan_knobs* force = nullptr);
 
 // The axis-vote plan of a single solve of n pairs on a G x G grid on device dev: T row bands
 // (row0[T + 1]), S circle slices, the largest band tile in bytes and the device's SM count.

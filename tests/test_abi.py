@@ -55,6 +55,7 @@ def test_struct_layouts_match_c(libpath, tmp_path):
         "sizeof(sprot_params), sizeof(sprot_rotation), sizeof(sprot_debug), sizeof(sprot_instance),"
         "sizeof(sprot_server_cfg), sizeof(sprot_request), sizeof(sprot_result),"
         "offsetof(sprot_params, tau), offsetof(sprot_rotation, cell_row), offsetof(sprot_result, t_submit_ms));"
+        "printf(\"%zu %zu\\n\", sizeof(sprot_plan_knobs), offsetof(sprot_plan_knobs, ms_tuned));"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
@@ -62,8 +63,33 @@ def test_struct_layouts_match_c(libpath, tmp_path):
     want = [ctypes.sizeof(binding.Params), ctypes.sizeof(binding.Rotation), ctypes.sizeof(binding.Debug),
             ctypes.sizeof(binding.Instance), ctypes.sizeof(binding.ServerCfg),
             ctypes.sizeof(binding.Request), ctypes.sizeof(binding.Result),
-            binding.Params.tau.offset, binding.Rotation.cell_row.offset, binding.Result.t_submit_ms.offset]
+            binding.Params.tau.offset, binding.Rotation.cell_row.offset, binding.Result.t_submit_ms.offset,
+            ctypes.sizeof(binding.Knobs), binding.Knobs.ms_tuned.offset]
     assert got == want
+
+
+def test_plan_knobs_without_gpu(libpath):
+    """The default knobs, and the tuned-plan query without a device (nothing tuned: the
+    defaults); the tuners check their arguments before any CUDA call."""
+    lib = binding.load(libpath)
+    assert binding.default_knobs() == {"vote_rounds": 1, "chunk_div": 600, "batch_slice": 32768,
+                                       "batch_div": 1200, "ms_tuned": 0.0, "ms_default": 0.0}
+    binding.autotune_reset()
+    found, k = binding.tuned_plan(10**6, 512)
+    assert not found and k == binding.default_knobs()
+    p = binding.make_params()
+    kn = binding.Knobs()
+    for reps in (0, 16):
+        assert lib.sprot_autotune_plan(FAKE, FAKE, 1000, ctypes.byref(p), reps, ctypes.byref(kn), None) == binding.E_INVAL
+    assert lib.sprot_autotune_plan(FAKE, FAKE, 0, ctypes.byref(p), 3, ctypes.byref(kn), None) == binding.E_INVAL
+    assert lib.sprot_autotune_batch(None, 4, 3, ctypes.byref(kn), None) == binding.E_INVAL
+    for field, value in (("vote_rounds", 0), ("vote_rounds", 4), ("chunk_div", 99), ("chunk_div", 2401),
+                         ("batch_slice", 16383), ("batch_slice", 65536), ("batch_div", 299), ("batch_div", 4801)):
+        bad = binding.Knobs(1, 600, 32768, 1200, 0.0, 0.0)
+        setattr(bad, field, value)
+        assert lib.sprot_set_tuned_plan(1000, 256, 0, ctypes.byref(bad)) == binding.E_INVAL
+    good = binding.Knobs(1, 600, 32768, 1200, 0.0, 0.0)
+    assert lib.sprot_set_tuned_plan(1000, 100, 0, ctypes.byref(good)) == binding.E_INVAL  # G not a power of two
 
 
 def test_invalid_arguments_rejected_without_gpu(libpath):
