@@ -359,6 +359,12 @@ typedef struct sprot_result {
  * completes each request independently. Errors: E_INVAL, E_NOMEM, E_CUDA. */
 int sprot_server_create(const sprot_server_cfg* cfg, sprot_server** out);
 
+/* Device bytes the server's admission counts for a request against device_budget_bytes: its
+ * inputs (24 bytes a pair) and the largest workspace any plan within the autotuner's knob
+ * ranges gives it, solved alone or in a batch (cfg is read for its device). 0 for a request
+ * the server would reject as invalid. */
+size_t sprot_server_request_bytes(const sprot_server_cfg* cfg, const sprot_request* req);
+
 /* Queues a request; *ticket identifies it. E_NOMEM if the request alone exceeds the budget;
  * E_BUSY if the queue is full or the server is stopping; E_INVAL for bad parameters. */
 int sprot_server_submit(sprot_server* s, const sprot_request* req, uint64_t* ticket);

@@ -30,7 +30,7 @@ EXPORTS = [
     "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
     "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan", "sprot_axis_vote_noalloc",
     "sprot_default_knobs", "sprot_autotune_plan", "sprot_autotune_batch", "sprot_tuned_plan",
-    "sprot_set_tuned_plan", "sprot_autotune_reset",
+    "sprot_set_tuned_plan", "sprot_autotune_reset", "sprot_server_request_bytes",
 ]
 
 
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH):
     lib.sprot_autotune_reset.argtypes = []
     lib.sprot_autotune_reset.restype = None
     lib.sprot_server_create.argtypes = [C.POINTER(ServerCfg), C.POINTER(vp)]
+    lib.sprot_server_request_bytes.argtypes = [C.POINTER(ServerCfg), C.POINTER(Request)]
+    lib.sprot_server_request_bytes.restype = C.c_size_t
     lib.sprot_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
     lib.sprot_server_wait.argtypes = [vp, C.c_uint64, i32, C.POINTER(Result)]
     lib.sprot_server_destroy.argtypes = [vp]
@@ -467,10 +469,16 @@ class Server:
     def __init__(self, budget_bytes: int, max_batch: int = 256, max_queue: int = 65536, device: int = 0):
         self.lib = load()
         cfg = ServerCfg(int(budget_bytes), int(max_batch), int(max_queue), int(device))
+        self.cfg = cfg
         h = C.c_void_p()
         check(self.lib.sprot_server_create(C.byref(cfg), C.byref(h)), "sprot_server_create")
         self.h = h
         self._keep = {}
+
+    def request_bytes(self, P: np.ndarray, Q: np.ndarray, params: Params) -> int:
+        """Bytes the admission counts for this request against the budget."""
+        req = Request(_ptr(P), _ptr(Q), P.shape[0], params)
+        return int(self.lib.sprot_server_request_bytes(C.byref(self.cfg), C.byref(req)))
 
     def submit(self, P: np.ndarray, Q: np.ndarray, params: Params) -> int:
         _check_points(P, Q)

@@ -167,10 +167,11 @@ void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_ba
   *n_bands = 0;
 }
 
-// Shared bytes per accumulator row (or column) of a band: the curve vote's tile holds G/2 words
-// per row of a row band (two rows share a word) and per column of a column band; the eps-band
-// vote's tile G/2 words per row.
-inline int vote_row_bytes(int G) { return 2 * G; }
+// Shared bytes per accumulator row (or column) of a band: the curve vote's tile holds G + 4
+// words per row pair of a row band (two rows share a word; 4 words of padding) and G + 1
+// half-words per column of a column band (two columns share a word; one row of padding);
+// the eps-band vote's tile G/2 words per row.
+inline int vote_row_bytes(int G) { return 2 * G + 8; }
 inline int eps_row_bytes(int G) { return 2 * G; }
 
 struct InstPlan {
@@ -416,11 +417,9 @@ void release_workspace(cudaStream_t st) {
   // call returns)
 }
 
-size_t problem_footprint(int64_t n, int G, int J, int k) {
+size_t problem_footprint(int64_t n, int G, int J, int k, int dev) {
   // the most slices any plan within the knobs' ranges gives the problem: alone (three rounds of
   // the SMs) or in a batch (slices of 16384 circles); at most one per-pair item per 256 pairs
-  int dev = 0;
-  cudaGetDevice(&dev);
   InstPlan ip{};
   ip.G = G;
   plan_vote(ip, n, true, sm_count(dev), false, INT64_MAX, 3);

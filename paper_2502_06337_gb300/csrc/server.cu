@@ -65,9 +65,17 @@ struct sprot_server {
 
 namespace {
 
-size_t request_bytes(const sprot_request& r) {
+size_t request_bytes(const sprot_request& r, int dev) {
   int G = r.params.grid ? r.params.grid : sprot_autotune_grid(r.n);
-  return (size_t)r.n * 24 + problem_footprint(r.n, G, r.params.angle_bins, r.params.k);
+  return (size_t)r.n * 24 + problem_footprint(r.n, G, r.params.angle_bins, r.params.k, dev);
+}
+
+bool request_valid(const sprot_request& r) {
+  const sprot_params& p = r.params;
+  const int G = p.grid ? p.grid : sprot_autotune_grid(r.n);
+  return r.P && r.Q && r.n >= 1 && !(G & (G - 1)) && G >= SPROT_MIN_GRID && G <= SPROT_MAX_GRID &&
+         p.angle_bins >= 2 && p.angle_bins <= SPROT_MAX_ANGLE_BINS && p.k >= 1 && p.k <= SPROT_MAX_K &&
+         p.tau > 0.0 && p.gate_window >= -1 && p.angle_window >= 0 && p.nms_deg >= 0.f;
 }
 
 }  // namespace
@@ -196,17 +204,16 @@ int sprot_server_create(const sprot_server_cfg* cfg, sprot_server** out) {
   return SPROT_OK;
 }
 
+size_t sprot_server_request_bytes(const sprot_server_cfg* cfg, const sprot_request* req) {
+  if (!cfg || !req || !request_valid(*req)) return 0;
+  return request_bytes(*req, cfg->device);
+}
+
 int sprot_server_submit(sprot_server* s, const sprot_request* req, uint64_t* ticket) {
-  if (!s || !req || !ticket || !req->P || !req->Q || req->n < 1) return SPROT_E_INVAL;
-  const sprot_params& p = req->params;
-  int G = p.grid ? p.grid : sprot_autotune_grid(req->n);
-  if ((G & (G - 1)) || G < SPROT_MIN_GRID || G > SPROT_MAX_GRID || p.angle_bins < 2 ||
-      p.angle_bins > SPROT_MAX_ANGLE_BINS || p.k < 1 || p.k > SPROT_MAX_K || !(p.tau > 0.0) ||
-      p.gate_window < -1 || p.angle_window < 0 || !(p.nms_deg >= 0.f))
-    return SPROT_E_INVAL;
+  if (!s || !req || !ticket || !request_valid(*req)) return SPROT_E_INVAL;
   auto r = std::make_shared<Req>();
   r->r = *req;
-  r->bytes = request_bytes(*req);
+  r->bytes = request_bytes(*req, s->cfg.device);
   std::lock_guard<std::mutex> g(s->mu);
   if (s->init_status != SPROT_OK) return s->init_status;
   if (r->bytes > s->cfg.device_budget_bytes) return SPROT_E_NOMEM;

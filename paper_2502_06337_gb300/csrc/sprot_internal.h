@@ -118,8 +118,9 @@ bool single_vote_plan(int64_t n, int G, int dev, int* T, int32_t* row0, int* S, 
 // Frees the solve() workspace of stream st (call before destroying st).
 void release_workspace(cudaStream_t st);
 
-// Device bytes one problem occupies in a solve() workspace (inputs excluded).
-size_t problem_footprint(int64_t n, int G, int J, int k);
+// Device bytes one problem may occupy in a solve() workspace on device dev (inputs excluded):
+// the most that any plan within the autotuner's knob ranges takes, alone or in a batch.
+size_t problem_footprint(int64_t n, int G, int J, int k, int dev);
 
 // ---- launchers -------------------------------------------------------------------------
 // Axis vote (vote_runs.cu). tile_bytes: the largest band's two tiles (4 G bytes per row); the

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
       }
     }
     __syncthreads();
-    flush_row_pair_tile(tile, G, R0, R1, D.partial + (int64_t)I.slice * G * (G >> 1));
+    flush_row_pair_tile(tile, G, G, R0, R1, D.partial + (int64_t)I.slice * G * (G >> 1));
     __syncthreads();
   }
 }

@@ -68,11 +68,14 @@ constexpr int kTab = kRec * 32;
 
 // The work item's part of the grid: rows [R0, R1) x columns [C0, C1) (a band of rows for the
 // row caps, a band of columns for the column caps) and its shared tile at byte address tb: for
-// rows, (R1 - R0)/2 x G words (word (i, j) holds rows R0 + 2i and R0 + 2i + 1 of column j); for
-// columns, G x W words with W = (C1 - C0)/2 (word (i, j) holds columns C0 + 2j and C0 + 2j + 1
-// of row i).
+// rows, (R1 - R0)/2 x RS words, RS = G + 4 (word (i, j) holds rows R0 + 2i and R0 + 2i + 1 of
+// column j); for columns, (G + 1) x W words with W = (C1 - C0)/2 (word (i, j) holds columns
+// C0 + 2j and C0 + 2j + 1 of row i). The extra column of a row tile and the extra row of a
+// column tile take the -1 of a run that ends on the grid's last cell, so no vote tests for it;
+// they are never read.
 struct Band {
   int G, R0, R1, C0, C1, W;
+  int RS;  // words per row pair of a row tile (G plus a pad of 4 that takes a run's end beyond the grid)
   float step, half;
   uint32_t tb;
 };
@@ -181,7 +184,7 @@ __device__ __forceinline__ void prepare(const Band& B, float d1, float d2, float
     if (ROWS && d1 == 0.f) {  // F = 2 d2 v: the rows on both sides of v = 0, whole
       for (int r = G / 2 - 1; r <= G / 2; ++r)
         if (r >= B.R0 && r < B.R1)
-          red_add(B.tb + 4u * (uint32_t)(((r - B.R0) >> 1) * G), ((r - B.R0) & 1) ? 0x10000u : 1u);
+          red_add(B.tb + 4u * (uint32_t)(((r - B.R0) >> 1) * B.RS), ((r - B.R0) & 1) ? 0x10000u : 1u);
     }
     if (!ROWS && d2 == 0.f) {  // F = 2 d1 u: the columns on both sides of u = 0, whole
       for (int c = G / 2 - 1; c <= G / 2; ++c)
@@ -309,7 +312,8 @@ __device__ __forceinline__ void store_rec(uint32_t* tab, int lane, const Prepare
 struct Walker {
   int len;                        // units of the segment (0: idle)
   float C, a2, absa, bT;
-  float kfl, knl, kfh, knh;       // lower root = kfl t + knl T/t, upper root = kfh t + knh T/t
+  float kfl, knl, kfh, knh;       // cell coordinates (root + 1) G/2 of the lower root
+                                  // kfl t + knl T/t + G/2 and of the upper kfh t + knh T/t + G/2
   float y, dy;                    // the next (narrower) line and its step
   int lw, hw;                     // cells of the crossings with the wider line
   bool ew;                        // the curve reaches the wider line
@@ -325,8 +329,8 @@ __device__ __forceinline__ bool line_cells(const Walker& w, float y, float half,
   const float s = disc * rsqrt_approx(fmaxf(disc, 1e-30f));
   const float t = w.absa + s;  // > 0: absa carries a tiny offset
   const float nr = T * rcp_approx(t);
-  lo = __float2int_rd(fmaf(fmaf(w.kfl, t, w.knl * nr), half, half));
-  hi = __float2int_rd(fmaf(fmaf(w.kfh, t, w.knh * nr), half, half));
+  lo = __float2int_rd(fmaf(w.kfl, t, fmaf(w.knl, nr, half)));
+  hi = __float2int_rd(fmaf(w.kfh, t, fmaf(w.knh, nr, half)));
   return disc >= 0.f;
 }
 
@@ -375,22 +379,24 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.a2 = a * a;
   w.absa = fabsf(a) + 1e-30f;
   w.bT = 2.f * bw;
-  // roots of C x^2 + 2 a x - T: lower -t/C and upper T/t for a >= 0, else -T/t and t/C
+  // roots of C x^2 + 2 a x - T: lower -t/C and upper T/t for a >= 0, else -T/t and t/C, in
+  // cells (scaled by G/2, a power of two)
   const float invC = C > 0.f ? __frcp_rn(C) : __int_as_float(0x7f800000);
   const bool apos = a >= 0.f;
-  w.kfl = apos ? -invC : 0.f;
-  w.knl = apos ? 0.f : -1.f;
-  w.kfh = apos ? 0.f : invC;
-  w.knh = apos ? 1.f : 0.f;
+  const float hs = B.half;
+  w.kfl = apos ? -invC * hs : 0.f;
+  w.knl = apos ? 0.f : -hs;
+  w.kfh = apos ? 0.f : invC * hs;
+  w.knh = apos ? hs : 0.f;
   w.dy = dm > 0 ? B.step : -B.step;
   const float yw = fmaf((float)(dm > 0 ? m : m + 1), B.step, -1.f);  // the first unit's wider line
   w.y = yw + w.dy;
   if (ROWS) {
     w.cl = 0;
     w.cr = G - 1;
-    w.ub = B.tb + 4u * (uint32_t)(((m - B.R0) >> 1) * G);
+    w.ub = B.tb + 4u * (uint32_t)(((m - B.R0) >> 1) * B.RS);
     w.inc = ((m - B.R0) & 1) ? 0x10000u : 1u;
-    w.pstep = dm > 0 ? 4 * G : -4 * G;
+    w.pstep = dm > 0 ? 4 * B.RS : -4 * B.RS;
   } else {
     const uint32_t clip = tab[7 * 32 + k];
     w.cl = (int)(clip & 0xffffu);
@@ -412,7 +418,6 @@ template <bool ROWS>
 __device__ __forceinline__ void step_walker(Walker& w, int i, const Band& B, uint32_t dummy) {
   int ln, hn;
   const bool en = line_cells(w, w.y, B.half, ln, hn);
-  const int lim = B.G - 1;  // the run axis spans the grid (columns for rows, rows for columns)
   const uint32_t xs = ROWS ? 4u : 4u * (uint32_t)B.W;
   const int b1 = en ? min(ln, max(hn, -(1 << 30)) - 1) : w.hw;
   const int a2 = en ? hn : (1 << 30);
@@ -420,12 +425,12 @@ __device__ __forceinline__ void step_walker(Walker& w, int i, const Band& B, uin
   const int x2 = max(a2, w.cl), y2 = min(w.hw, w.cr);
   const bool act = (i < w.len) && w.ew;
   const bool v1 = act && x1 <= y1, v2 = act && x2 <= y2;
-  const bool e1 = v1 && y1 < lim, e2 = v2 && y2 < lim;
   const uint32_t ninc = 0u - w.inc;
+  // a run ending on the grid's last cell puts its -inc in the tile's pad (y + 1 = G)
   red_add(v1 ? w.ub + (uint32_t)x1 * xs : dummy, w.inc);
-  red_add(e1 ? w.ub + (uint32_t)(y1 + 1) * xs : dummy, ninc);
+  red_add(v1 ? w.ub + (uint32_t)(y1 + 1) * xs : dummy, ninc);
   red_add(v2 ? w.ub + (uint32_t)x2 * xs : dummy, w.inc);
-  red_add(e2 ? w.ub + (uint32_t)(y2 + 1) * xs : dummy, ninc);
+  red_add(v2 ? w.ub + (uint32_t)(y2 + 1) * xs : dummy, ninc);
   w.lw = ln;
   w.hw = hn;
   w.ew = en;
@@ -499,7 +504,8 @@ __device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, u
   B.half = 0.5f * (float)G;
   uint32_t* tile = smem;
   B.tb = (uint32_t)__cvta_generic_to_shared(tile);
-  const int words = ROWS ? ((B.R1 - B.R0) >> 1) * G : G * B.W;
+  B.RS = G + 4;
+  const int words = ROWS ? ((B.R1 - B.R0) >> 1) * B.RS : G * B.W;
   uint4* t4 = reinterpret_cast<uint4*>(tile);
   for (int x = threadIdx.x; x < (words >> 2); x += blockDim.x) t4[x] = make_uint4(0, 0, 0, 0);
   __syncthreads();
@@ -538,7 +544,7 @@ __device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, u
 
   uint32_t* out = D.partial + (int64_t)I.slice * G * W2;
   if (ROWS) {
-    flush_row_pair_tile(tile, G, B.R0, B.R1, out);
+    flush_row_pair_tile(tile, G, B.RS, B.R0, B.R1, out);
   } else {
     // prefix sums down each word column in chunks of rows (a thread per column and chunk), the
     // chunks' carries, then the rows

@@ -212,9 +212,10 @@ def test_concurrent_calls_on_separate_streams(lib):
 
 
 def test_server_budget_admits_one_request_at_a_time(lib):
-    """Six requests of n = 20,000 at G = 128 (about 0.7 MB each with their workspace) under a
-    1 MB budget: each fits alone but no two fit together, so the server must queue them, admit
-    one at a time as memory frees up, and still give every request its result alone."""
+    """Six requests of n = 20,000 at G = 128 under a budget of 1.5 times the bytes the admission
+    counts for one of them: each fits alone but no two fit together, so the server must queue
+    them, admit one at a time as memory frees up, and still give every request its result
+    alone."""
     import torch
 
     from paper_2502_06337_gb300 import binding as B
@@ -222,7 +223,10 @@ def test_server_budget_admits_one_request_at_a_time(lib):
     probs = [synth.make_problem(20000, (0.3,), 0.01, seed=80 + i) for i in range(6)]
     prm = B.make_params(grid=128, angle_bins=360, tau=0.05)
     alone = [B.estimate_rotation(torch.from_numpy(p.P).cuda(), torch.from_numpy(p.Q).cuda(), prm) for p in probs]
-    with B.Server(1 << 20, max_batch=8) as srv:
+    with B.Server(1 << 40, max_batch=8) as probe:
+        one = probe.request_bytes(probs[0].P, probs[0].Q, prm)
+    assert one > 20000 * 24
+    with B.Server(one * 3 // 2, max_batch=8) as srv:
         tickets = [srv.submit(p.P, p.Q, prm) for p in probs]
         got = [srv.wait(t) for t in tickets]
     spans = []
