@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="sprot", choices=["sprot", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated extras to run (multi_rotation, paper_recipe, ls_axis, "
+                         "sampled_vote, eps_vote, batched, served) or 'all'")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the oracle CPU baseline (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=0,
@@ -309,34 +312,21 @@ def run_sprot(args):
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(prob, G, J, tau, args.cpu_sample)
         if not args.no_extras:
-            try:
-                out["multi_rotation"] = run_multi(B, dev)
-            except Exception as e:
-                out["multi_rotation"] = {"error": repr(e)}
-            try:
-                out["paper_recipe"] = run_paper_recipe(B, dev)
-            except Exception as e:
-                out["paper_recipe"] = {"error": repr(e)}
-            try:
-                out["ls_axis"] = run_ls_axis(B, dev)
-            except Exception as e:
-                out["ls_axis"] = {"error": repr(e)}
-            try:
-                out["sampled_vote"] = run_sampled(B, P, Q, G)
-            except Exception as e:
-                out["sampled_vote"] = {"error": repr(e)}
-            try:
-                out["eps_vote"] = run_eps(B, P, Q, G)
-            except Exception as e:
-                out["eps_vote"] = {"error": repr(e)}
-            try:
-                out["batched"] = run_batched(B, dev)
-            except Exception as e:  # report, never hide
-                out["batched"] = {"error": repr(e)}
-            try:
-                out["served"] = run_served(B)
-            except Exception as e:
-                out["served"] = {"error": repr(e)}
+            extras = [("multi_rotation", lambda: run_multi(B, dev)),
+                      ("paper_recipe", lambda: run_paper_recipe(B, dev)),
+                      ("ls_axis", lambda: run_ls_axis(B, dev)),
+                      ("sampled_vote", lambda: run_sampled(B, P, Q, G)),
+                      ("eps_vote", lambda: run_eps(B, P, Q, G)),
+                      ("batched", lambda: run_batched(B, dev)),
+                      ("served", lambda: run_served(B))]
+            wanted = None if args.extras == "all" else set(args.extras.split(","))
+            for name, fn in extras:
+                if wanted is not None and name not in wanted:
+                    continue
+                try:
+                    out[name] = fn()
+                except Exception as e:  # report, never hide
+                    out[name] = {"error": repr(e)}
         print(json.dumps(out), flush=True)
     barrier(world)
     if world > 1:

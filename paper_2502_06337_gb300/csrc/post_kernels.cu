@@ -488,54 +488,95 @@ __device__ __forceinline__ double warp_sum16(const double (&v)[16], int lane) {
   return a1 + __shfl_xor_sync(kFull, a1, 1);
 }
 
+// ---- float-float sums of q p^T ---------------------------------------------------------
+//
+// FP64 instructions run on GB300 at about two lanes per clock per SM, so the per-pair sums of
+// the rotation passes are carried as unevaluated pairs of float32 (hi + lo, about 48
+// significant bits), on the FP32 pipes: a product of two float32 values splits exactly into
+// hi = fl(a b) and lo = a b - hi (one FMA), and two pairs add by Knuth's two-sum of the high
+// parts with the low parts folded into its error term, then renormalised (Dekker's
+// double-length addition). The explicitly rounded intrinsics keep the compiler from fusing or
+// reassociating these steps. Only the last block's solve converts the totals to FP64.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, t);
+  return FF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  const float h = __fmul_rn(a, b);
+  return FF{h, fmaf(a, b, -h)};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF v, int o) {
+  return FF{__shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.lo, o)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
+
+// Warp sums of 16 per-lane float-float values by recursive halving (as warp_sum16). Lane l
+// returns the total of value (l >> 1) & 15.
+__device__ __forceinline__ FF warp_sum16_ff(const FF (&v)[16], int lane) {
+  FF a8[8], a4[4], a2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a8[j] = ff_add(h16 ? v[8 + j] : v[j], ff_shfl_xor(h16 ? v[j] : v[8 + j], 16));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a4[j] = ff_add(h8 ? a8[4 + j] : a8[j], ff_shfl_xor(h8 ? a8[j] : a8[4 + j], 8));
+#pragma unroll
+  for (int j = 0; j < 2; ++j) a2[j] = ff_add(h4 ? a4[2 + j] : a4[j], ff_shfl_xor(h4 ? a4[j] : a4[2 + j], 4));
+  const FF a1 = ff_add(h2 ? a2[1] : a2[0], ff_shfl_xor(h2 ? a2[0] : a2[1], 2));
+  return ff_add(a1, ff_shfl_xor(a1, 1));
+}
+
 // Block sum of acc[K][10] into out[kf][10] (fixed order: warps in index order). All threads
 // call; the rotation loop is unrolled so that acc stays in registers.
 template <int K>
-__device__ __forceinline__ void block_sums(double (&acc)[K][10], int kf, double* out) {
-  __shared__ double s[kStreamThreads / 32][10];
+__device__ __forceinline__ void block_sums(FF (&acc)[K][10], int kf, float2* out) {
+  __shared__ FF s[kStreamThreads / 32][10];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int a = 0; a < K; ++a) {
     if (a >= kf) break;
-    double v16[16];
+    FF v16[16];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) v16[t] = t < 10 ? acc[a][t] : 0.0;
-    const double tot = warp_sum16(v16, l);
+    for (int t = 0; t < 16; ++t) v16[t] = t < 10 ? acc[a][t] : FF{0.f, 0.f};
+    const FF tot = warp_sum16_ff(v16, l);
     if ((l & 1) == 0 && (l >> 1) < 10) s[w][l >> 1] = tot;
     __syncthreads();
     if (threadIdx.x < 10) {
-      double v = 0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += s[i][threadIdx.x];
-      out[a * 10 + threadIdx.x] = v;
+      FF v{0.f, 0.f};
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v = ff_add(v, s[i][threadIdx.x]);
+      out[a * 10 + threadIdx.x] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
   }
 }
 
-// q p^T of pair i added to acc[0..8] in FP64 (the float32 products are exact in FP64).
-__device__ __forceinline__ void add_qpT(double* acc, const float* __restrict__ P,
-                                        const float* __restrict__ Q, int64_t i) {
-  const double p0 = __ldg(P + 3 * i), p1 = __ldg(P + 3 * i + 1), p2 = __ldg(P + 3 * i + 2);
-  const double q0 = __ldg(Q + 3 * i), q1 = __ldg(Q + 3 * i + 1), q2 = __ldg(Q + 3 * i + 2);
-  acc[0] = fma(q0, p0, acc[0]);
-  acc[1] = fma(q0, p1, acc[1]);
-  acc[2] = fma(q0, p2, acc[2]);
-  acc[3] = fma(q1, p0, acc[3]);
-  acc[4] = fma(q1, p1, acc[4]);
-  acc[5] = fma(q1, p2, acc[5]);
-  acc[6] = fma(q2, p0, acc[6]);
-  acc[7] = fma(q2, p1, acc[7]);
-  acc[8] = fma(q2, p2, acc[8]);
+// q p^T of pair i added to acc[0..8] (each float32 product split exactly into hi + lo).
+__device__ __forceinline__ void add_qpT(FF* acc, const float* __restrict__ P, const float* __restrict__ Q,
+                                        int64_t i) {
+  const float p[3] = {__ldg(P + 3 * i), __ldg(P + 3 * i + 1), __ldg(P + 3 * i + 2)};
+  const float q[3] = {__ldg(Q + 3 * i), __ldg(Q + 3 * i + 1), __ldg(Q + 3 * i + 2)};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[3 * r + c] = ff_add(acc[3 * r + c], ff_prod(q[r], p[c]));
 }
 
-// Per-warp queues of selected pairs, one per rotation. FP64 arithmetic runs on GB300 at a
-// small fraction of the FP32 rate and costs the same per warp instruction whatever the number
-// of active lanes, so the sums are taken over full warps of selected pairs: a pair is queued
-// (as its offset in the work item) when selected, and each time a queue holds 32 pairs the
-// whole warp adds them.
+// Per-warp queues of selected pairs, one per rotation: a pair is queued (as its offset in the
+// work item) when selected, and each time a queue holds 32 pairs the whole warp adds them, so
+// that the sums run over full warps.
 template <int K>
 struct PairQueues {
-  double acc[K][10];
+  FF acc[K][10];
   int len[K];    // warp-uniform queue lengths
   int total[K];  // warp-uniform counts of selected pairs
   int* q;        // this warp's queues: [K][64] in shared memory
@@ -546,7 +587,7 @@ struct PairQueues {
     for (int a = 0; a < K; ++a) {
       len[a] = total[a] = 0;
 #pragma unroll
-      for (int t = 0; t < 10; ++t) acc[a][t] = 0.0;
+      for (int t = 0; t < 10; ++t) acc[a][t] = FF{0.f, 0.f};
     }
   }
   // Queue pair i0 + off for rotation a if sel (called by the whole warp with a uniform a).
@@ -573,9 +614,9 @@ struct PairQueues {
 #pragma unroll
     for (int a = 0; a < K; ++a)
       if (lane < len[a]) add_qpT(acc[a], D.P, D.Q, i0 + q[a * 64 + lane]);
-    // the pair count travels in slot 9, once per warp
+    // the pair count travels in slot 9, once per warp (exact in float32: at most an item's pairs)
 #pragma unroll
-    for (int a = 0; a < K; ++a) acc[a][9] = lane == 0 ? (double)total[a] : 0.0;
+    for (int a = 0; a < K; ++a) acc[a][9] = FF{lane == 0 ? (float)total[a] : 0.f, 0.f};
   }
 };
 
@@ -1100,27 +1141,31 @@ __device__ void solve_rotation(const InstDev& D, int a, int phase, const double*
 // concurrently, rotation a on lane 0 of warp a.
 static_assert(kStreamThreads / 32 >= kMaxK, "one warp per rotation");
 __device__ __noinline__ void kabsch_all(const InstDev& D, int kf, int phase) {
-  __shared__ double part[kStreamThreads][10];
+  __shared__ FF part[kStreamThreads][10];
   __shared__ double tot[kMaxK][10];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int a = 0; a < kf; ++a) {
-    double v[10];
+    FF v[10];
 #pragma unroll
-    for (int t = 0; t < 10; ++t) v[t] = 0.0;
-    const double* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
+    for (int t = 0; t < 10; ++t) v[t] = FF{0.f, 0.f};
+    const float2* base = D.msum + ((int64_t)phase * D.n_items * D.k + a) * 10;
     for (int it = threadIdx.x; it < D.n_items; it += blockDim.x) {
-      const double* src = base + (int64_t)it * D.k * 10;
+      const float2* src = base + (int64_t)it * D.k * 10;
 #pragma unroll
-      for (int t = 0; t < 10; ++t) v[t] += __ldcg(src + t);
+      for (int t = 0; t < 10; ++t) {
+        const float2 x = __ldcg(src + t);
+        v[t] = ff_add(v[t], FF{x.x, x.y});
+      }
     }
 #pragma unroll
     for (int t = 0; t < 10; ++t) part[threadIdx.x][t] = v[t];
     __syncthreads();
     for (int col = w; col < 10; col += nw) {
-      double x = 0.0;
-      for (int i = l; i < (int)blockDim.x; i += 32) x += part[i][col];
-      x = warp_sum_d(x);
-      if (l == 0) tot[a][col] = x;
+      FF x{0.f, 0.f};
+      for (int i = l; i < (int)blockDim.x; i += 32) x = ff_add(x, part[i][col]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
+      if (l == 0) tot[a][col] = ff_to_double(x);
     }
     __syncthreads();
   }

@@ -642,7 +642,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     d.peak_key = reinterpret_cast<unsigned long long*>(D + ip.o_peak);
     d.hist = (pb.dbg && pb.dbg->hist) ? nullptr : reinterpret_cast<uint32_t*>(D + ip.o_hist);
     d.bins = (pb.dbg && pb.dbg->bins) ? pb.dbg->bins : reinterpret_cast<int16_t*>(D + ip.o_bins);
-    d.msum = reinterpret_cast<double*>(D + ip.o_msum);
+    d.msum = reinterpret_cast<float2*>(D + ip.o_msum);
     d.item0 = ip.item0;
     d.n_items = ip.n_items;
     d.n_found = reinterpret_cast<int32_t*>(D + ip.o_nfound);

@@ -56,7 +56,8 @@ struct InstDev {
   unsigned long long* peak_key;  // [k] packed (count, ~index) maxima
   uint32_t* hist;                // [k][J]
   int16_t* bins;                 // [k][n]
-  double* msum;                  // [2][n_items][k][10]: 9 sums of q p^T and a count
+  float2* msum;                  // [2][n_items][k][10]: 9 sums of q p^T and a count, each a
+                                 // float-float (hi, lo)
   int32_t item0, n_items;        // this instance's per-pair work items
   int32_t* n_found;              // device int
   uint32_t* n_deg;               // device count of degenerate pairs
