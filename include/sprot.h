@@ -19,12 +19,11 @@
  * Conventions shared by every entry point
  *   - P and Q are n x 3 row-major float32 arrays (x, y, z of each point). They are device
  *     pointers unless the call's flags contain SPROT_HOST_PTRS, in which case they (and the
- *     per-pair output arrays) are host pointers. Pageable host inputs are copied to the
- *     device before the solve. Inputs in pinned, device-mapped host memory (cudaHostAlloc,
- *     cudaMallocHost, cudaHostRegister) are read by the axis vote directly over the host
- *     link while a second stream copies them to the device for the later passes; such calls
- *     are replayed from a CUDA graph keyed by the host addresses when they repeat. The
- *     library reads P and Q only; the caller owns them and every output buffer.
+ *     per-pair output arrays) are host pointers, copied to the device at the start of the
+ *     solve. Calls with inputs in pinned host memory (cudaHostAlloc, cudaMallocHost,
+ *     cudaHostRegister) are replayed from a CUDA graph keyed by the host addresses when they
+ *     repeat; pageable inputs run directly. The library reads P and Q only; the caller owns
+ *     them and every output buffer.
  *   - Grid cell (row, col) spans u in [-1 + 2 col/G, -1 + 2 (col+1)/G] and v likewise for
  *     row; cells are closed, so a circle on a shared edge counts in both cells. Grids are
  *     row-major uint32 [row][col].

@@ -121,8 +121,6 @@ extern "C" int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n
   InstDev& d = s.inst;
   d.P = P;
   d.Q = Q;
-  d.Pv = P;  // the vote reads its pairs through Pv/Qv
-  d.Qv = Q;
   d.n = n;
   d.G = G;
   d.k = 1;

@@ -99,18 +99,19 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 // The device address of a host buffer of `bytes` bytes when all of it lies in one pinned,
 // device-mapped allocation (cudaHostAlloc / cudaMallocHost / cudaHostRegister); else null.
-const float* mapped_host(const void* p, size_t bytes) {
+// True when [p, p + bytes) lies in one pinned host allocation (cudaHostAlloc, cudaMallocHost or
+// cudaHostRegister): a copy from it may be captured in a CUDA graph.
+bool pinned_host(const void* p, size_t bytes) {
   cudaPointerAttributes a{}, b{};
   const char* last = static_cast<const char*>(p) + bytes - 1;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return false;
   }
   if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
-    return nullptr;
-  if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
-    return nullptr;  // not one contiguous mapping
-  return static_cast<const float*>(a.devicePointer);
+    return false;
+  // one contiguous mapping
+  return static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) == (ptrdiff_t)(bytes - 1);
 }
 
 int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, int k) {
@@ -212,7 +213,8 @@ struct Workspace {
   // events recorded around the vote kernel inside every captured sequence (solves on a
   // workspace are serialised and synchronised, so one pair serves all its graphs)
   cudaEvent_t tv0 = nullptr, tv1 = nullptr;
-  // second stream for host-input copies that overlap the axis vote, with its fork/join events
+  // second stream for the second half of a host problem's input copy (under the first half's
+  // vote), with its fork and join events
   cudaStream_t aux = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   bool aux_stream() {
@@ -495,6 +497,11 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     tuned_lookup(tune_key(ws->device, m > 1, m > 1 ? total_n / m : probs[0].n,
                           probs[0].prm.grid ? probs[0].prm.grid : sprot_autotune_grid(probs[0].n)),
                  &kn);
+  // One large problem from host buffers: its input copy is split in two, the vote's items of
+  // the first half of the slices run as soon as the first half is copied, and the second half
+  // is copied under them (two rounds of items at least, so that each half fills the SMs).
+  const bool split = m == 1 && probs[0].host_io && probs[0].n >= (1 << 18) && ws->aux_stream();
+  if (split) kn.vote_rounds = std::max(kn.vote_rounds, 2);
   // slice-reduction items: 512 words (one 16-byte column per thread) for one problem; in a
   // batch about 64 x 512 word-slices per item (an item reads every slice of its words), between
   // 512 and 8192 words
@@ -541,11 +548,22 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     max_J = std::max(max_J, ip.J);
   }
   // Longest vote items first (the persistent CTAs then finish together).
-  std::stable_sort(vitems.begin(), vitems.end(), [&](const VoteItem& a, const VoteItem& b) {
-    double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
-    double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
-    return wa > wb;
-  });
+  // (one problem: items stay in slice order, which the split copy relies on)
+  if (m > 1)
+    std::stable_sort(vitems.begin(), vitems.end(), [&](const VoteItem& a, const VoteItem& b) {
+      double wa = (double)(a.c1 - a.c0) * plan[a.inst].G / plan[a.inst].T;
+      double wb = (double)(b.c1 - b.c0) * plan[b.inst].G / plan[b.inst].T;
+      return wa > wb;
+    });
+  // split copy: the items of the first half of the slices, and the pairs they read
+  int n_first = (int)vitems.size();
+  int64_t pairs_first = total_n;
+  if (split) {
+    const int half = plan[0].S / 2;
+    n_first = 0;
+    while (n_first < (int)vitems.size() && vitems[n_first].slice % plan[0].S < half) ++n_first;
+    pairs_first = n_first > 0 ? vitems[n_first - 1].c1 : 0;
+  }
 
   // ---- layout -------------------------------------------------------------------------
   size_t off = 0;
@@ -560,7 +578,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
   const size_t o_sit = take(sizeof(StreamItem) * sitems.size());
   const size_t header_end = off;
   const size_t o_zero = off;
-  const size_t o_counter = take(sizeof(int));
+  const size_t o_counter = take(2 * sizeof(int));  // the vote's item counters (two with a split copy)
   for (auto& ip : plan) {
     ip.o_peak = take(sizeof(unsigned long long) * ip.k);
     ip.o_hist = take(sizeof(uint32_t) * ip.k * ip.J);
@@ -594,24 +612,15 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
   char* D = ws->dev;
   char* H = ws->host;
 
-  // Host inputs in pinned, device-mapped memory: the axis vote reads them directly over the
-  // host link while a second stream copies them to the device for the later passes, so the
-  // copy overlaps the vote. Other host inputs are copied first.
-  std::vector<std::pair<const float*, const float*>> vote_src(m, {nullptr, nullptr});
-  bool overlap = false;
+  // Host inputs are copied to the workspace at the start of the launch sequence. Copies from
+  // pinned host memory can be captured in the sequence's graph (keyed by the host addresses);
+  // pageable ones run directly. (The vote reads every pair once per band and orientation, so
+  // it reads the device copy: reading pinned memory over the host link made it 65% slower.)
+  std::vector<bool> pinned(m, false);
   for (int i = 0; i < m; ++i) {
     const Problem& pb = probs[i];
-    if (!pb.host_io) continue;
-    const float* pv = mapped_host(pb.P, (size_t)pb.n * 12);
-    const float* qv = mapped_host(pb.Q, (size_t)pb.n * 12);
-    if (pv && qv) {
-      vote_src[i] = {pv, qv};
-      overlap = true;
-    }
-  }
-  if (overlap && !ws->aux_stream()) {
-    overlap = false;
-    vote_src.assign(m, {nullptr, nullptr});
+    if (pb.host_io)
+      pinned[i] = pinned_host(pb.P, (size_t)pb.n * 12) && pinned_host(pb.Q, (size_t)pb.n * 12);
   }
 
   // ---- tables -------------------------------------------------------------------------
@@ -623,8 +632,6 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     std::memset(&d, 0, sizeof(d));
     d.P = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_P) : pb.P;
     d.Q = pb.host_io ? reinterpret_cast<const float*>(D + ip.o_Q) : pb.Q;
-    d.Pv = vote_src[i].first ? vote_src[i].first : d.P;
-    d.Qv = vote_src[i].second ? vote_src[i].second : d.Q;
     d.n = ip.n;
     d.G = ip.G;
     d.J = ip.J;
@@ -672,14 +679,10 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
   // Caller pointers outside the workspace are baked into a graph. Debug exports and pageable
   // host inputs run directly; pinned host inputs (and outputs) are part of the graph's key.
   bool direct_only = !graphs || !ws->timing_events();
-  for (int i = 0; i < m; ++i) direct_only |= probs[i].dbg != nullptr || (probs[i].host_io && !vote_src[i].first);
+  for (int i = 0; i < m; ++i) direct_only |= probs[i].dbg != nullptr || (probs[i].host_io && !pinned[i]);
   std::optional<VoteTimer> vt;
   auto enqueue = [&](bool direct) -> bool {
     bool ok = true;
-    if (overlap) {  // the second stream starts after everything already ordered on st
-      ok &= ck(cudaEventRecord(ws->fork, st));
-      ok &= ck(cudaStreamWaitEvent(ws->aux, ws->fork, 0));
-    }
     ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
     ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
     for (int i = 0; i < m; ++i) {
@@ -687,24 +690,37 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
       if (pb.dbg && pb.dbg->hist)
         ok &= ck(cudaMemsetAsync(pb.dbg->hist, 0, sizeof(uint32_t) * plan[i].k * plan[i].J, st));
       if (pb.host_io) {
-        cudaStream_t cs = vote_src[i].first ? ws->aux : st;
-        ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, (size_t)pb.n * 12, cudaMemcpyHostToDevice, cs));
-        ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, (size_t)pb.n * 12, cudaMemcpyHostToDevice, cs));
+        const size_t b0 = (size_t)(split ? pairs_first : pb.n) * 12;  // the first (or only) part
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_P, pb.P, b0, cudaMemcpyHostToDevice, st));
+        ok &= ck(cudaMemcpyAsync(D + plan[i].o_Q, pb.Q, b0, cudaMemcpyHostToDevice, st));
       }
     }
-    if (overlap) ok &= ck(cudaEventRecord(ws->join, ws->aux));
     if (!ok) return false;
+    if (split) ok &= ck(cudaEventRecord(ws->fork, st));  // the first part is on the device
     if (direct)
       vt.emplace(st);
     else
       ok &= ck(cudaEventRecord(ws->tv0, st));
-    launch_axis_vote_runs(dvit, (int)vitems.size(), dinst, dcounter,
-                          std::min((int)vitems.size(), nsm), vote_tile, st);
+    launch_axis_vote_runs(dvit, n_first, dinst, dcounter, std::min(n_first, nsm), vote_tile, st);
+    if (split) {
+      // the second part, copied under the first items' vote (after the first part, so that the
+      // two copies do not share the link)
+      const Problem& pb = probs[0];
+      const size_t b0 = (size_t)pairs_first * 12, b1 = (size_t)(pb.n - pairs_first) * 12;
+      ok &= ck(cudaStreamWaitEvent(ws->aux, ws->fork, 0));
+      ok &= ck(cudaMemcpyAsync(D + plan[0].o_P + b0, reinterpret_cast<const char*>(pb.P) + b0, b1,
+                               cudaMemcpyHostToDevice, ws->aux));
+      ok &= ck(cudaMemcpyAsync(D + plan[0].o_Q + b0, reinterpret_cast<const char*>(pb.Q) + b0, b1,
+                               cudaMemcpyHostToDevice, ws->aux));
+      ok &= ck(cudaEventRecord(ws->join, ws->aux));
+      ok &= ck(cudaStreamWaitEvent(st, ws->join, 0));
+      const int n_second = (int)vitems.size() - n_first;
+      launch_axis_vote_runs(dvit + n_first, n_second, dinst, dcounter + 1, std::min(n_second, nsm), vote_tile, st);
+    }
     if (direct)
       vt->stop(st);
     else
       ok &= ck(cudaEventRecord(ws->tv1, st));
-    if (overlap) ok &= ck(cudaStreamWaitEvent(st, ws->join, 0));  // the later passes read P, Q
     // each kernel's last block per instance finishes that instance's stage (peaks; angle peak
     // and Rodrigues; the two Kabsch solves)
     launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
@@ -732,7 +748,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     const std::vector<uint64_t> key = {
         (uint64_t)(uintptr_t)D, (uint64_t)(uintptr_t)H, header_end, o_zero, zero_end, o_res, res_end,
         vitems.size(), ritems.size(), sitems.size(), (uint64_t)m, (uint64_t)max_k, (uint64_t)max_J,
-        (uint64_t)vote_tile, (uint64_t)nsm};
+        (uint64_t)vote_tile, (uint64_t)nsm, (uint64_t)split, (uint64_t)pairs_first};
     std::vector<uint64_t> k2 = key;
     for (int i = 0; i < m; ++i) {
       if (!probs[i].host_io) continue;
@@ -829,8 +845,6 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   std::memset(&d, 0, sizeof(d));
   d.P = P;
   d.Q = Q;
-  d.Pv = P;
-  d.Qv = Q;
   d.n = n;
   d.G = G;
   d.k = 1;

@@ -5,9 +5,9 @@
 // the device-memory budget from the front of the queue (admission; a batch holds at most
 // kServerBatchPairs pairs), copy their inputs to the device and solve them together with one
 // launch sequence. While one worker's batch is on the GPU another admits the requests that
-// arrived meanwhile and launches them on its own stream, so consecutive batches overlap. Each request completes on its own (a waiter is
-// woken per request), and its result depends only on its own inputs: instances share no
-// accumulator and no floating-point reduction.
+// arrived meanwhile and launches them on its own stream, so consecutive batches overlap. Each
+// request completes on its own (a waiter is woken per request), and its result depends only on
+// its own inputs: instances share no accumulator and no floating-point reduction.
 #include <chrono>
 #include <condition_variable>
 #include <deque>

@@ -36,12 +36,8 @@ struct DevRot {
 
 // One problem of a (possibly single-element) batch, as the kernels see it.
 struct InstDev {
-  const float* P;
+  const float* P;  // device memory (the caller's, or the workspace copy of host inputs)
   const float* Q;
-  // the axis vote's source of P and Q: P and Q, or the caller's pinned host buffers, which the
-  // vote reads over the host link while P and Q are being copied to the device
-  const float* Pv;
-  const float* Qv;
   int64_t n;
   int32_t G, J, k, w, window;
   int32_t n_bands, S;            // bands and partial slices of the axis vote (the curve vote

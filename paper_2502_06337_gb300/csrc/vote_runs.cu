@@ -510,8 +510,8 @@ __device__ __forceinline__ void vote_item(const VoteItem& I, const InstDev& D, u
   for (int x = threadIdx.x; x < (words >> 2); x += blockDim.x) t4[x] = make_uint4(0, 0, 0, 0);
   __syncthreads();
 
-  const float* __restrict__ P = D.Pv;  // device memory, or pinned host memory (see InstDev)
-  const float* __restrict__ Q = D.Qv;
+  const float* __restrict__ P = D.P;
+  const float* __restrict__ Q = D.Q;
   const int64_t count = I.c1 - I.c0;
   int base = 0;
   if (lane == 0) base = atomicAdd(s_next, 32);
