@@ -983,15 +983,18 @@ __device__ bool polar_cayley_f32(const double* Xd, const float* q0, double* q) {
 // residual that the iteration drives to zero) and the quaternion are carried in FP64; H and
 // the 3 x 3 solve need no more than float32, whose relative error in w only adds a factor
 // 1 + 1e-7 cond to the quadratic convergence. q is left unnormalised until the end (a scale
-// of U scales v and H alike and leaves w unchanged). From a float32 start three steps reach
-// the FP64 rounding floor. Returns false if the system is not positive definite or the last
-// correction is not below 5e-12 (the iteration did not settle). The loop ends once a correction
-// is below 1e-12: the error left is then of the order of its square.
+// of U scales v and H alike and leaves w unchanged). The loop ends after the step whose
+// correction has |w|^2 < 1e-13: the error left is then of the order of |w|^2 + 1e-7 cond |w|,
+// about 1e-13 rad, four orders below the 1e-9 to which the rotations are held. From a
+// float32-accurate start (|w| about 1e-7) that is the first step; each FP64 instruction of a
+// single thread costs tens of cycles on this part, so the step that would only confirm it is
+// not taken. Returns false if the system is not positive definite or no step settled within
+// four.
 __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
   float Xf[9];
   for (int t = 0; t < 9; ++t) Xf[t] = (float)X[t];
   float n2 = 1.f;
-  for (int it = 0; it < 4 && n2 >= 1e-24f; ++it) {
+  for (int it = 0; it < 4 && n2 >= 1e-13f; ++it) {
     quat_to_rot(q, R);  // |q|^2 times a rotation
     // v in FP64
     const double v0 = (R[2] * X[1] + R[5] * X[4] + R[8] * X[7]) - (R[1] * X[2] + R[4] * X[5] + R[7] * X[8]);
@@ -1026,7 +1029,7 @@ __device__ bool polar_refine_f64(const double* X, double* q, double* R) {
   const double rn = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   for (int t = 0; t < 4; ++t) q[t] *= rn;
   quat_to_rot(q, R);
-  return n2 < 2.5e-23f;
+  return n2 < 1e-13f;
 }
 
 // phase 0: R_init from the vote-set sums; phase 1: R from the label sums, for rotation a of
@@ -1092,13 +1095,16 @@ __device__ void solve_rotation(const InstDev& D, int a, int phase, const double*
     const double det = s[0] * c0 + s[1] * c1 + s[2] * c2;
     const double n2 = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) +
                       (s[6] * s[6] + s[7] * s[7] + s[8] * s[8]);
-    // X = M 2^-e with the largest |entry| in [1, 2) (exact)
-    double mx = 0.0;
-    for (int t = 0; t < 9; ++t) mx = fmax(mx, fabs(s[t]));
-    const int e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
-    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+    // X = M 2^-e with the largest |entry| in [1, 2), exact, by integer arithmetic on the
+    // exponent fields (entries that would fall below the normal range become 0)
+    int emax = 0;
+    for (int t = 0; t < 9; ++t) emax = max(emax, (int)((__double_as_longlong(s[t]) >> 52) & 0x7ff));
+    const int e = emax - 1023;
     double X[9];
-    for (int t = 0; t < 9; ++t) X[t] = s[t] * sc;
+    for (int t = 0; t < 9; ++t) {
+      const long long b = __double_as_longlong(s[t]);
+      X[t] = (int)((b >> 52) & 0x7ff) - e > 0 ? __longlong_as_double(b - ((long long)e << 52)) : 0.0;
+    }
     double q[4];
     // the start: the nearby rotation the previous stage found (R_vote for the vote set, R_init for
     // the inliers), carried to float32 precision by float32 Cayley steps; the scaled Newton
