@@ -3,6 +3,7 @@
 // refinement with labels.
 #include <math_constants.h>
 
+#include "pdl.cuh"
 #include "sprot_internal.h"
 
 namespace sprot {
@@ -137,9 +138,11 @@ constexpr int kReduceGroups = kReduceThreads / 32;
 __global__ void __launch_bounds__(kReduceThreads)
     k_grid_reduce(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts) {
   __shared__ uint32_t part[kReduceGroups][256];
+  pdl_launch_dependents();
   const ReduceItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   const int G = D.G, W = G >> 1, S = D.S;
+  pdl_wait();  // the partials
   const int64_t stride = (int64_t)G * W / 4;  // uint4 per slice
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   unsigned long long best = 0;
@@ -221,6 +224,8 @@ __device__ __forceinline__ bool is_peak(const uint32_t* __restrict__ grid, int G
 // suppression radius from every axis taken in the earlier rounds.
 __global__ void __launch_bounds__(256)
     k_nms_round(const ReduceItem* __restrict__ items, const InstDev* __restrict__ insts, int round) {
+  pdl_launch_dependents();
+  pdl_wait();  // the grid and the peak keys
   const ReduceItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   if (round >= D.k) return;
@@ -362,9 +367,14 @@ __global__ void __launch_bounds__(kStreamThreads)
   __shared__ Window win[kMaxK];
   __shared__ int s_found;
   __shared__ unsigned s_deg;
+  pdl_launch_dependents();
   const StreamItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   const int J = D.J;
+  // the first pair's loads (the inputs) go out before the wait for the peaks
+  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (I.i0 + threadIdx.x < I.i1) load_raw(D, I.i0 + threadIdx.x, nx);
+  pdl_wait();
   if (threadIdx.x == 0) {
     s_found = *D.n_found;
     s_deg = 0;
@@ -394,8 +404,6 @@ __global__ void __launch_bounds__(kStreamThreads)
   unsigned ndeg = 0;
   // each thread's pairs i, i + blockDim, ...: the next pair's loads are issued before the
   // current pair is processed
-  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (I.i0 + threadIdx.x < I.i1) load_raw(D, I.i0 + threadIdx.x, nx);
   for (int64_t i = I.i0 + threadIdx.x; i < I.i1; i += blockDim.x) {
     float cur[6];
 #pragma unroll
@@ -624,6 +632,8 @@ struct PairQueues {
 template <int K>
 __global__ void __launch_bounds__(kStreamThreads, 4)
     k_vote_set_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  pdl_launch_dependents();
+  pdl_wait();  // the angle peaks and the pairs' bins
   const StreamItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   __shared__ int bhat[kMaxK];
@@ -671,24 +681,26 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
 template <int K>
 __global__ void __launch_bounds__(kStreamThreads, 4)
     k_label_sum(const StreamItem* __restrict__ items, const InstDev* __restrict__ insts) {
+  pdl_launch_dependents();
   const StreamItem I = items[blockIdx.x];
   const InstDev& D = insts[I.inst];
   __shared__ float Rf[kMaxK][9];
   __shared__ int s_found;
   __shared__ int queues[kStreamThreads / 32][K * 64];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  // each warp takes 32 consecutive pairs per iteration; the next iteration's loads are issued
+  // before the current pairs are processed (the first before the wait for R_init)
+  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (I.i0 + 32 * wp + lane < I.i1) load_raw(D, I.i0 + 32 * wp + lane, nx);
+  pdl_wait();
   if (threadIdx.x == 0) s_found = *D.n_found;
   __syncthreads();
   const int kf = s_found;
   if (threadIdx.x < kf * 9) Rf[threadIdx.x / 9][threadIdx.x % 9] = D.rot[threadIdx.x / 9].R_init_f[threadIdx.x % 9];
   __syncthreads();
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   PairQueues<K> pq;
   pq.init(queues[wp]);
   const float tau2 = D.tau * D.tau;
-  // each warp takes 32 consecutive pairs per iteration; the next iteration's loads are issued
-  // before the current pairs are processed
-  float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (I.i0 + 32 * wp + lane < I.i1) load_raw(D, I.i0 + 32 * wp + lane, nx);
   for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
     const int64_t i = base + lane;
     const bool valid = i < I.i1;
@@ -1346,13 +1358,13 @@ void launch_write_peaks(const InstDev* insts, int32_t* cells, uint32_t* counts, 
 
 void launch_grid_reduce(const ReduceItem* items, int n_items, const InstDev* insts,
                         cudaStream_t st) {
-  k_grid_reduce<<<n_items, kReduceThreads, 0, st>>>(items, insts);
+  launch_dependent(k_grid_reduce, n_items, kReduceThreads, 0, st, items, insts);
   launches_add(1);
 }
 
 void launch_nms_round(const ReduceItem* items, int n_items, const InstDev* insts, int round,
                       cudaStream_t st) {
-  k_nms_round<<<n_items, 256, 0, st>>>(items, insts, round);
+  launch_dependent(k_nms_round, n_items, 256, 0, st, items, insts, round);
   launches_add(1);
 }
 
@@ -1360,33 +1372,33 @@ void launch_angle_vote(const StreamItem* items, int n_items, const InstDev* inst
                        int max_J, cudaStream_t st) {
   size_t smem = (size_t)max_k * max_J * sizeof(uint32_t);
   if (smem > 48 * 1024) ensure_dynamic_smem(reinterpret_cast<const void*>(k_angle_vote), (int)smem);
-  k_angle_vote<<<n_items, kStreamThreads, smem, st>>>(items, insts, max_J);
+  launch_dependent(k_angle_vote, n_items, kStreamThreads, smem, st, items, insts, max_J);
   launches_add(1);
 }
 
 void launch_vote_set_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                          cudaStream_t st) {
   if (max_k <= 1)
-    k_vote_set_sum<1><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_vote_set_sum<1>, n_items, kStreamThreads, 0, st, items, insts);
   else if (max_k <= 2)
-    k_vote_set_sum<2><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_vote_set_sum<2>, n_items, kStreamThreads, 0, st, items, insts);
   else if (max_k <= 4)
-    k_vote_set_sum<4><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_vote_set_sum<4>, n_items, kStreamThreads, 0, st, items, insts);
   else
-    k_vote_set_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_vote_set_sum<kMaxK>, n_items, kStreamThreads, 0, st, items, insts);
   launches_add(1);
 }
 
 void launch_label_sum(const StreamItem* items, int n_items, const InstDev* insts, int max_k,
                       cudaStream_t st) {
   if (max_k <= 1)
-    k_label_sum<1><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_label_sum<1>, n_items, kStreamThreads, 0, st, items, insts);
   else if (max_k <= 2)
-    k_label_sum<2><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_label_sum<2>, n_items, kStreamThreads, 0, st, items, insts);
   else if (max_k <= 4)
-    k_label_sum<4><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_label_sum<4>, n_items, kStreamThreads, 0, st, items, insts);
   else
-    k_label_sum<kMaxK><<<n_items, kStreamThreads, 0, st>>>(items, insts);
+    launch_dependent(k_label_sum<kMaxK>, n_items, kStreamThreads, 0, st, items, insts);
   launches_add(1);
 }
 

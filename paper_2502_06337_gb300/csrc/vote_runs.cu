@@ -46,6 +46,7 @@
 // float32 roundings of zero: inside the band in which the closed-cell test may go either way.
 #include <stdint.h>
 
+#include "pdl.cuh"
 #include "row_tiles.cuh"
 #include "sprot_internal.h"
 
@@ -584,6 +585,7 @@ __global__ void __launch_bounds__(kRunThreads, 1)
                      int* __restrict__ counter, int tile_words) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int s_item, s_next;
+  pdl_launch_dependents();  // the slice reduction may be scheduled on the SMs this grid frees
   for (;;) {
     if (threadIdx.x == 0) {
       s_item = atomicAdd(counter, 1);
