@@ -381,8 +381,8 @@ __device__ __forceinline__ void start_walker(const Band& B, const uint32_t* tab,
   w.absa = fabsf(a) + 1e-30f;
   w.bT = 2.f * bw;
   // roots of C x^2 + 2 a x - T: lower -t/C and upper T/t for a >= 0, else -T/t and t/C, in
-  // cells (scaled by G/2, a power of two)
-  const float invC = C > 0.f ? __frcp_rn(C) : __int_as_float(0x7f800000);
+  // cells (scaled by G/2, a power of two); 1/C by the hardware approximation, like 1/t
+  const float invC = C > 0.f ? rcp_approx(C) : __int_as_float(0x7f800000);
   const bool apos = a >= 0.f;
   const float hs = B.half;
   w.kfl = apos ? -invC * hs : 0.f;
