@@ -178,9 +178,9 @@ def test_host_pointers_match_device(lib):
 
 @pytest.mark.parametrize("n,offset", [(5000, 0), (5000, 777), (1_000_000, 0)])
 def test_pinned_host_pointers_match_device(lib, n, offset):
-    """Host inputs in pinned memory are read by the axis vote directly while a second stream
-    copies them to the device; the results must equal the device-pointer solve. ``offset``
-    places the buffers inside a larger pinned allocation."""
+    """Host inputs in pinned memory (copied by the solve's launch sequence, replayed from a
+    graph; at n = 10^6 the copy is split in two under the vote): the results must equal the
+    device-pointer solve. ``offset`` places the buffers inside a larger pinned allocation."""
     from paper_2502_06337_gb300 import binding as B
     import torch
 
@@ -200,6 +200,37 @@ def test_pinned_host_pointers_match_device(lib, n, offset):
         assert a["axis_votes"] == b["axis_votes"] and a["angle_votes"] == b["angle_votes"]
         assert np.array_equal(a["R"], b["R"])
         assert np.array_equal(mask_d.cpu().numpy(), mask_h.numpy())
+
+
+@pytest.mark.parametrize("n,pinned,k", [((1 << 18) - 1, True, 1), ((1 << 18) + 17, True, 1),
+                                         ((1 << 18) + 17, False, 1), (300_001, False, 2)])
+def test_split_host_copy_matches_device(lib, n, pinned, k):
+    """A large problem from host buffers (n >= 2^18) copies its first half, votes the first
+    round of items while the second half is copied on a second stream, then votes the rest:
+    results, labels and the exported grid equal the device-pointer solve bit for bit, for odd
+    n, pinned and pageable inputs, just below and above the threshold, and with k = 2."""
+    from paper_2502_06337_gb300 import binding as B
+    import torch
+
+    fr = (0.1,) if k == 1 else (0.1, 0.1)
+    prob = synth.make_problem(n, fr, 0.01, seed=n % 97)
+    prm = B.make_params(grid=512, angle_bins=720, k=k, nms_deg=2.0, tau=0.052)
+    lab_d = torch.zeros(n, dtype=torch.int32, device="cuda")
+    a = B.estimate_rotations(torch.from_numpy(prob.P).cuda(), torch.from_numpy(prob.Q).cuda(), prm, labels=lab_d)
+    if pinned:
+        Ph, Qh = torch.from_numpy(prob.P).pin_memory().numpy(), torch.from_numpy(prob.Q).pin_memory().numpy()
+        lab_h = torch.zeros(n, dtype=torch.int32).pin_memory().numpy()
+    else:
+        Ph, Qh, lab_h = prob.P.copy(), prob.Q.copy(), np.zeros(n, np.int32)
+    prm.flags = B.HOST_PTRS
+    for _ in range(3):  # direct, then (pinned) captured as a graph and replayed
+        b = B.estimate_rotations(Ph, Qh, prm, labels=lab_h)
+        assert len(a) == len(b) == k
+        for x, y in zip(a, b):
+            assert (x["cell"], x["bin"], x["n_inliers"], x["axis_votes"]) == (y["cell"], y["bin"], y["n_inliers"],
+                                                                             y["axis_votes"])
+            assert np.array_equal(x["R"], y["R"]) and np.array_equal(x["R_init"], y["R_init"])
+        assert np.array_equal(lab_d.cpu().numpy(), lab_h)
 
 
 def test_pinned_host_buffers_reused_with_new_contents_and_sizes(lib):
