@@ -588,47 +588,50 @@ def run_eps(B, P, Q, G, reps=5):
 
 
 def run_batched(B, dev, m=4096):
-    """4096 uneven instances in one batched solve, with the default plan and with the plan the
-    autotuner picks for the batch's class, against a per-instance loop of single solves over all
-    4096 instances."""
+    """4096 uneven instances in one batched solve (packed: all pairs back to back in one tensor,
+    with offsets), with the default plan and with the plan the autotuner picks for the batch's
+    class; the same batch through the list form (one tensor pair per instance); and a
+    per-instance loop of single solves over all 4096 instances."""
     import torch
 
     from paper_2502_06337_gb300 import synth
 
     specs = synth.batch_specs(m, seed=0)
-    probs, total = [], 0
-    for s in specs:
-        pb = synth.make_problem(s["n"], s["inlier_fracs"], s["sigma"], seed=s["seed"])
-        tau = synth.default_tau(s["sigma"])
-        P = torch.from_numpy(pb.P).to(dev)
-        Q = torch.from_numpy(pb.Q).to(dev)
-        probs.append((P, Q, B.make_params(grid=0, angle_bins=360, tau=tau), pb))
-        total += s["n"]
-    batch = [(P, Q, prm) for P, Q, prm, _ in probs]
+    probs = [synth.make_problem(s["n"], s["inlier_fracs"], s["sigma"], seed=s["seed"]) for s in specs]
+    off = np.concatenate([[0], np.cumsum([s["n"] for s in specs])]).astype(np.int64)
+    total = int(off[-1])
+    P_all = torch.from_numpy(np.concatenate([pb.P for pb in probs])).to(dev)
+    Q_all = torch.from_numpy(np.concatenate([pb.Q for pb in probs])).to(dev)
+    taus = np.array([synth.default_tau(s["sigma"]) for s in specs])
+    prm = B.params_array(m, grid=0, angle_bins=360, tau=taus)
     reps = 3
 
-    def time_batch():
-        B.estimate_batch(batch)  # warm-up (workspace, graph capture)
-        B.estimate_batch(batch)
+    def timed(call):
+        call()  # warm-up (workspace, graph capture)
+        call()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
-            res, grids = B.estimate_batch(batch)
-        return (time.perf_counter() - t0) / reps, res, grids
+            out = call()
+        return (time.perf_counter() - t0) / reps, out
 
     B.autotune_reset()
-    t_batch, res, grids = time_batch()
-    knobs = B.autotune_batch(batch, reps=2)
-    t_tuned, res_t, _ = time_batch()
+    t_batch, (res, grids) = timed(lambda: B.estimate_batch_packed(P_all, Q_all, off, prm))
+    views = [(P_all[off[i]:off[i + 1]], Q_all[off[i]:off[i + 1]]) for i in range(m)]
+    lst = [(P, Q, B.make_params(grid=0, angle_bins=360, tau=float(taus[i]))) for i, (P, Q) in enumerate(views)]
+    t_list, (res_l, _) = timed(lambda: B.estimate_batch(lst))
+    knobs = B.autotune_batch_packed(P_all, Q_all, off, prm, reps=2)
+    t_tuned, (res_t, _) = timed(lambda: B.estimate_batch_packed(P_all, Q_all, off, prm))
     B.autotune_reset()
     # per-instance loop of the plain single solve on every instance (same params and G)
-    for P, Q, prm, _ in probs[:8]:
-        B.estimate_rotations(P, Q, B.make_params(grid=grids[0], angle_bins=360, tau=prm.tau), allow_noaxis=True)
+    for i in range(8):
+        B.estimate_rotations(*views[i], B.make_params(grid=int(grids[i]), angle_bins=360, tau=float(taus[i])),
+                             allow_noaxis=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     loop_res = []
-    for i, (P, Q, prm, _) in enumerate(probs):
-        p1 = B.make_params(grid=grids[i], angle_bins=360, tau=prm.tau)
+    for i, (P, Q) in enumerate(views):
+        p1 = B.make_params(grid=int(grids[i]), angle_bins=360, tau=float(taus[i]))
         loop_res.append(B.estimate_rotations(P, Q, p1, allow_noaxis=True))
     t_loop = time.perf_counter() - t0
     # integer results identical; FP64 rotations equal up to summation order (max |dR|; the
@@ -640,9 +643,13 @@ def run_batched(B, dev, m=4096):
                                             float(np.max(np.abs(x["R"] - y["R"]))) < 1e-9 for x, y in zip(a, b))
                    for a, b in zip(ra, rb))
 
-    errs = [math.degrees(_rot_err(pb.rotations[0], r[0]["R"])) for (_, _, _, pb), r in zip(probs, res) if r]
+    errs = [math.degrees(_rot_err(pb.rotations[0], r[0]["R"])) for pb, r in zip(probs, res) if r]
     return {"instances": m, "correspondences": total, "batch_s": t_batch,
             "solves_per_s": m / t_batch, "Mcorr_per_s": total / t_batch / 1e6,
+            "form": "packed: one P and one Q tensor, offsets, a params record array",
+            "list_form": {"solves_per_s": m / t_list, "batch_s": t_list,
+                          "note": "one tensor pair and Params per instance (per-instance Python marshalling)",
+                          "same_results": bool(same(res_l, res))},
             "tuned": {"knobs": {k: knobs[k] for k in ("batch_slice", "batch_div")},
                       "solves_per_s": m / t_tuned, "batch_s": t_tuned,
                       "tuner_ms_default": knobs["ms_default"], "tuner_ms_tuned": knobs["ms_tuned"],

@@ -367,10 +367,26 @@ class BatchResult:
         return (self._one(i) for i in range(len(self)))
 
 
+_PARAMS_DTYPE = None
+
+
+def _params_dtype():
+    """numpy dtype of one sprot_params, so that a list of Params converts in one pass."""
+    global _PARAMS_DTYPE
+    if _PARAMS_DTYPE is None:
+        f = _struct_dtype(Params)
+        _PARAMS_DTYPE = np.dtype({"names": [x[0] for x in f], "formats": [x[1] for x in f],
+                                  "offsets": [x[2] for x in f], "itemsize": C.sizeof(Params)})
+    return _PARAMS_DTYPE
+
+
 def _instance_table(problems):
     """The sprot_instance table of a batch as one numpy record array in the layout of
-    sprot_instance (a batch of thousands costs no per-field Python work), with the output
-    arrays it points into: (table, rotations, n_found, kmax)."""
+    sprot_instance, with the output arrays it points into: (table, rotations, n_found, kmax).
+    A batch of thousands costs a few list passes and no per-field Python work: the Params
+    structures are converted from their raw bytes in one step."""
+    import torch
+
     global _INSTANCE_FIELDS
     if _INSTANCE_FIELDS is None:
         _INSTANCE_FIELDS = _struct_dtype(Instance)
@@ -378,33 +394,102 @@ def _instance_table(problems):
     fields = _INSTANCE_FIELDS
     dt = np.dtype({"names": [f[0] for f in fields], "formats": [f[1] for f in fields],
                    "offsets": [f[2] for f in fields], "itemsize": C.sizeof(Instance)})
+    Ps = [pb[0] for pb in problems]
+    Qs = [pb[1] for pb in problems]
+    f32 = torch.float32
+    for P, Q in zip(Ps, Qs):
+        if not (isinstance(P, torch.Tensor) and isinstance(Q, torch.Tensor) and P.dtype is f32 and
+                Q.dtype is f32 and P.dim() == 2 and P.shape[1] == 3 and P.shape == Q.shape and
+                P.is_contiguous() and Q.is_contiguous()):
+            _check_points(P, Q)  # names the failure
+            raise ValueError("P and Q must be contiguous float32 tensors of shape (n, 3)")
+    prm = np.frombuffer(b"".join([bytes(pb[2]) for pb in problems]), dtype=_params_dtype())
+    kmax = max(1, int(prm["k"].max())) if m else 1
     tab = np.zeros(m, dtype=dt)
-    kmax = 1
-    for pb in problems:
-        kmax = max(kmax, int(pb[2].k))
+    tab["P"] = np.fromiter((P.data_ptr() for P in Ps), np.uint64, m)
+    tab["Q"] = np.fromiter((Q.data_ptr() for Q in Qs), np.uint64, m)
+    tab["n"] = np.fromiter((P.shape[0] for P in Ps), np.int64, m)
+    tab["labels"] = np.fromiter((pb[3].data_ptr() if len(pb) > 3 and pb[3] is not None else 0
+                                 for pb in problems), np.uint64, m)
+    for name in prm.dtype.names:
+        tab["params." + name] = prm[name]
     rot = np.zeros(m * kmax, dtype=_rotation_dtype())
     n_found = np.zeros(m, dtype=np.int32)
-    P_ptr = np.empty(m, dtype=np.uint64)
-    Q_ptr = np.empty(m, dtype=np.uint64)
-    L_ptr = np.zeros(m, dtype=np.uint64)
-    ns = np.empty(m, dtype=np.int64)
-    prm_cols = {name: np.empty(m, dtype=dt.fields["params." + name][0]) for name, _ in Params._fields_}
-    for i, pb in enumerate(problems):
-        P, Q, prm = pb[0], pb[1], pb[2]
-        _check_points(P, Q)
-        P_ptr[i] = P.data_ptr()
-        Q_ptr[i] = Q.data_ptr()
-        ns[i] = P.shape[0]
-        if len(pb) > 3 and pb[3] is not None:
-            L_ptr[i] = pb[3].data_ptr()
-        for name, _ in Params._fields_:
-            prm_cols[name][i] = getattr(prm, name)
-    tab["P"], tab["Q"], tab["n"], tab["labels"] = P_ptr, Q_ptr, ns, L_ptr
-    for name, col in prm_cols.items():
-        tab["params." + name] = col
     tab["out"] = rot.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(kmax * C.sizeof(Rotation))
     tab["n_found"] = n_found.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(4)
     return tab, rot, n_found, kmax
+
+
+def params_array(m: int, **fields) -> np.ndarray:
+    """m sprot_params as one numpy record array (the defaults of make_params, then ``fields``,
+    each a scalar or a length-m array), for the packed batch calls."""
+    arr = np.zeros(m, dtype=_params_dtype())
+    base = make_params()
+    for name, _ in Params._fields_:
+        arr[name] = fields.get(name, getattr(base, name))
+    return arr
+
+
+def _packed_table(P, Q, offsets, params, labels=None):
+    """The sprot_instance table of instances stored back to back: instance i is rows
+    offsets[i]:offsets[i + 1] of the device tensors P and Q (and of ``labels``, an n-element
+    int32 device tensor, if given). ``params``: one Params for every instance, or a record
+    array from params_array. Returns (table, rotations, n_found, kmax)."""
+    _check_points(P, Q)
+    off = np.asarray(offsets, dtype=np.int64)
+    m = len(off) - 1
+    if m < 1 or off[0] != 0 or off[-1] != P.shape[0] or np.any(np.diff(off) < 1):
+        raise ValueError("offsets must rise strictly from 0 to n")
+    if isinstance(params, Params):
+        prm = np.frombuffer(bytes(params) * m, dtype=_params_dtype())
+    else:
+        prm = np.asarray(params)
+        if prm.dtype != _params_dtype() or prm.shape != (m,):
+            raise ValueError("params: a Params or params_array(m, ...)")
+    if labels is not None and (labels.dtype != __import__("torch").int32 or labels.numel() != P.shape[0]
+                               or not labels.is_contiguous()):
+        raise ValueError("labels must be a contiguous int32 tensor of n elements")
+    global _INSTANCE_FIELDS
+    if _INSTANCE_FIELDS is None:
+        _INSTANCE_FIELDS = _struct_dtype(Instance)
+    fields = _INSTANCE_FIELDS
+    dt = np.dtype({"names": [f[0] for f in fields], "formats": [f[1] for f in fields],
+                   "offsets": [f[2] for f in fields], "itemsize": C.sizeof(Instance)})
+    kmax = max(1, int(prm["k"].max()))
+    tab = np.zeros(m, dtype=dt)
+    row = off[:-1].astype(np.uint64)
+    tab["P"] = np.uint64(P.data_ptr()) + row * np.uint64(12)
+    tab["Q"] = np.uint64(Q.data_ptr()) + row * np.uint64(12)
+    tab["n"] = np.diff(off)
+    tab["labels"] = 0 if labels is None else np.uint64(labels.data_ptr()) + row * np.uint64(4)
+    for name in prm.dtype.names:
+        tab["params." + name] = prm[name]
+    rot = np.zeros(m * kmax, dtype=_rotation_dtype())
+    n_found = np.zeros(m, dtype=np.int32)
+    tab["out"] = rot.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(kmax * C.sizeof(Rotation))
+    tab["n_found"] = n_found.ctypes.data + np.arange(m, dtype=np.uint64) * np.uint64(4)
+    return tab, rot, n_found, kmax
+
+
+def estimate_batch_packed(P, Q, offsets, params, labels=None, stream=None):
+    """sprot_estimate_batch over instances stored back to back in P and Q (see _packed_table):
+    the batch's table costs a few numpy operations whatever its size. Returns (BatchResult,
+    array of the grid sides used)."""
+    tab, rot, n_found, kmax = _packed_table(P, Q, offsets, params, labels)
+    st = load().sprot_estimate_batch(tab.ctypes.data_as(C.POINTER(Instance)), len(tab), _stream(stream))
+    check(st, "sprot_estimate_batch")
+    return BatchResult(rot, n_found, kmax), tab["params.grid"].copy()
+
+
+def autotune_batch_packed(P, Q, offsets, params, reps: int = 3, stream=None) -> dict:
+    """autotune_batch for a packed batch."""
+    tab, rot, n_found, _ = _packed_table(P, Q, offsets, params)
+    k = Knobs()
+    st = load().sprot_autotune_batch(tab.ctypes.data_as(C.POINTER(Instance)), len(tab), int(reps),
+                                     C.byref(k), _stream(stream))
+    del rot, n_found
+    check(st, "sprot_autotune_batch")
+    return k.to_dict()
 
 
 def estimate_batch(problems, stream=None):

@@ -135,7 +135,7 @@ int validate(const float* P, const float* Q, int64_t n, const sprot_params* p, i
 // random great circles cross the plane with density proportional to 2 / (1 + u^2 + v^2) (the
 // stereographic length element over the uniform density of the sphere), whose integral across a
 // row is (4 / a) atan(1 / a), a = sqrt(1 + v^2).
-void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_bands, int32_t* row0) {
+void plan_bands_uncached(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_bands, int32_t* row0) {
   constexpr int U = 8;  // rows per planning unit
   const int cap = (smem_bytes - table_bytes) / row_bytes;
   const int P = G / U, capp = cap / U;  // units in all, per band
@@ -166,6 +166,26 @@ void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_ba
   }
   // unreachable for G <= 2048 (cap >= 88 rows)
   *n_bands = 0;
+}
+
+// The band plan depends only on its four arguments and is needed once per instance of every
+// call (thousands in a batch): computed once per thread and key.
+void plan_bands(int G, int smem_bytes, int row_bytes, int table_bytes, int* n_bands, int32_t* row0) {
+  struct Entry {
+    int T;
+    std::vector<int32_t> row0;
+  };
+  thread_local std::map<std::array<int, 4>, Entry> cache;
+  const std::array<int, 4> key{G, smem_bytes, row_bytes, table_bytes};
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    Entry e;
+    e.row0.assign(kMaxBands + 1, 0);
+    plan_bands_uncached(G, smem_bytes, row_bytes, table_bytes, &e.T, e.row0.data());
+    it = cache.emplace(key, std::move(e)).first;
+  }
+  *n_bands = it->second.T;
+  for (int b = 0; b <= it->second.T; ++b) row0[b] = it->second.row0[b];
 }
 
 // Shared bytes per accumulator row (or column) of a band: the curve vote's tile holds G + 4

@@ -316,3 +316,27 @@ def test_release_stream_workspace_returns_memory(lib):
     free1 = torch.cuda.mem_get_info()[0]
     assert free0 - free1 < (64 << 20), f"{(free0 - free1) / 2**20:.0f} MiB not returned"
     B.release_stream_workspace(torch.cuda.current_stream().cuda_stream)  # no-op-safe on a used stream too
+
+
+def test_packed_batch_matches_list_batch(lib):
+    """The packed form (all pairs back to back, offsets, a params record array, one labels
+    tensor) gives every instance the results and labels of the list form."""
+    import torch
+
+    from paper_2502_06337_gb300 import binding as B
+
+    inst = [x for x in _instances() if x[1]["n"] > 1]
+    P = torch.from_numpy(np.concatenate([pb.P for pb, _ in inst])).cuda()
+    Q = torch.from_numpy(np.concatenate([pb.Q for pb, _ in inst])).cuda()
+    off = np.concatenate([[0], np.cumsum([pb.n for pb, _ in inst])])
+    arr = B.params_array(len(inst), grid=[s["grid"] for _, s in inst], angle_bins=360, k=[s["k"] for _, s in inst],
+                         nms_deg=2.0, tau=0.05)
+    lab = torch.full((int(off[-1]),), -7, dtype=torch.int32, device="cuda")
+    res, grids = B.estimate_batch_packed(P, Q, off, arr, labels=lab)
+    lst = [(P[off[i]:off[i + 1]], Q[off[i]:off[i + 1]], _params(B, s),
+            torch.full((pb.n,), -7, dtype=torch.int32, device="cuda")) for i, (pb, s) in enumerate(inst)]
+    ref, grids_l = B.estimate_batch(lst)
+    assert np.array_equal(grids, grids_l)
+    for i in range(len(inst)):
+        _same(res[i], ref[i], tol=0.0)
+        assert torch.equal(lab[off[i]:off[i + 1]], lst[i][3])
