@@ -334,10 +334,10 @@ __device__ __forceinline__ void pair_geom(const float* r, PairGeom& g) {
   float d1 = g.p0 - g.q0, d2 = g.p1 - g.q1, d3 = g.p2 - g.q2;
   float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
   g.deg = (m == 0.f);
-  int e = g.deg ? 0 : ilogbf(m);
-  g.d1 = scalbnf(d1, -e);
-  g.d2 = scalbnf(d2, -e);
-  g.d3 = scalbnf(d3, -e);
+  const float sc = inv_pow2_of(m);
+  g.d1 = d1 * sc;
+  g.d2 = d2 * sc;
+  g.d3 = d3 * sc;
 }
 
 // min / max of c2 x^2 + c1 x over [lo, hi].
@@ -1211,10 +1211,10 @@ __global__ void __launch_bounds__(kAxisThreads)
     float d1 = __ldg(P + 3 * i) - __ldg(Q + 3 * i);
     float d2 = __ldg(P + 3 * i + 1) - __ldg(Q + 3 * i + 1);
     float d3 = __ldg(P + 3 * i + 2) - __ldg(Q + 3 * i + 2);
-    const int e = ilogbf(fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3))));
-    d1 = scalbnf(d1, -e);
-    d2 = scalbnf(d2, -e);
-    d3 = scalbnf(d3, -e);
+    const float sc = inv_pow2_of(fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3))));
+    d1 *= sc;
+    d2 *= sc;
+    d3 *= sc;
     const float r = rsqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
     const double z1 = d1 * r, z2 = d2 * r, z3 = d3 * r;
     acc[0] = fma(z1, z1, acc[0]);

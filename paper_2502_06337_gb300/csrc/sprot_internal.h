@@ -34,6 +34,15 @@ struct DevRot {
   float q_init[4];        // unit quaternion of R_init (w, x, y, z): the start of the second solve
 };
 
+// 2^-e for the binary exponent e of a finite m > 0 (from the exponent field ex: 2^(127 - ex),
+// clamped to a normal number), so that m * inv_pow2_of(m) lies in [1, 2). A subnormal m
+// (ex = 0) gets 2^127, which brings it into the normal range. Multiplying by it is exact, so
+// every later float32 decision on the scaled values is the one on the unscaled values.
+__device__ __forceinline__ float inv_pow2_of(float m) {
+  const int ex = min((__float_as_int(m) >> 23) & 0xff, 253);
+  return __int_as_float((254 - ex) << 23);
+}
+
 // One problem of a (possibly single-element) batch, as the kernels see it.
 struct InstDev {
   const float* P;  // device memory (the caller's, or the workspace copy of host inputs)

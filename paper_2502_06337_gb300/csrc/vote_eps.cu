@@ -195,12 +195,12 @@ __global__ void __launch_bounds__(kEpsThreads, 1)
       float d3 = __ldg(D.P + 3 * i + 2) - __ldg(D.Q + 3 * i + 2);
       const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
       if (m == 0.f) continue;  // degenerate: no circle
-      const int e = ilogbf(m);
-      // -d gives the same band (F_minus and F_plus exchange and change sign)
-      const float sg = d3 < 0.f ? -1.f : 1.f;
-      d1 = sg * scalbnf(d1, -e);
-      d2 = sg * scalbnf(d2, -e);
-      d3 = sg * scalbnf(d3, -e);
+      // scaled to max |d_k| in [1, 2) and signed so that d3 >= 0 (-d gives the same band: F_minus
+      // and F_plus exchange and change sign)
+      const float sc = (d3 < 0.f ? -1.f : 1.f) * inv_pow2_of(m);
+      d1 *= sc;
+      d2 *= sc;
+      d3 *= sc;
       const float ed = eps * sqrtf(fmaf(d1, d1, fmaf(d2, d2, d3 * d3)));
       const float Cm = d3 - ed, Cp = d3 + ed;
       const float iCm = Cm != 0.f ? __frcp_rn(Cm) : 0.f, iCp = Cp != 0.f ? __frcp_rn(Cp) : 0.f;

@@ -280,10 +280,10 @@ __device__ __forceinline__ bool circle_from(const float* r, float& d1, float& d2
   d3 = r[2] - r[5];
   const float m = fmaxf(fabsf(d1), fmaxf(fabsf(d2), fabsf(d3)));
   if (m == 0.f) return false;
-  const int e = ilogbf(m);
-  d1 = scalbnf(d1, -e);
-  d2 = scalbnf(d2, -e);
-  d3 = scalbnf(d3, -e);
+  const float sc = inv_pow2_of(m);
+  d1 *= sc;
+  d2 *= sc;
+  d3 *= sc;
   if (d3 < 0.f) {
     d1 = -d1;
     d2 = -d2;
