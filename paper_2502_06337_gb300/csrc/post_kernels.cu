@@ -312,9 +312,10 @@ struct PairGeom {
 };
 
 // Raw p and q of pair i (six loads, independent of one another).
-__device__ __forceinline__ void load_raw(const InstDev& D, int64_t i, float* r) {
-  const float* p = D.P + 3 * i;
-  const float* q = D.Q + 3 * i;
+__device__ __forceinline__ void load_raw(const float* __restrict__ P, const float* __restrict__ Q, int64_t i,
+                                         float* r) {
+  const float* p = P + 3 * i;
+  const float* q = Q + 3 * i;
   r[0] = __ldg(p);
   r[1] = __ldg(p + 1);
   r[2] = __ldg(p + 2);
@@ -372,8 +373,15 @@ __global__ void __launch_bounds__(kStreamThreads)
   const InstDev& D = insts[I.inst];
   const int J = D.J;
   // the first pair's loads (the inputs) go out before the wait for the peaks
+  // the instance's fields the pair loop uses, held in registers (the loop's stores to the bins
+  // would otherwise make every iteration reload them)
+  const float* __restrict__ const Pp = D.P;
+  const float* __restrict__ const Qp = D.Q;
+  int16_t* __restrict__ const bins = D.bins;
+  const int64_t nn = D.n;
+  const int gw = D.w;
   float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (I.i0 + threadIdx.x < I.i1) load_raw(D, I.i0 + threadIdx.x, nx);
+  if (I.i0 + threadIdx.x < I.i1) load_raw(Pp, Qp, I.i0 + threadIdx.x, nx);
   pdl_wait();
   if (threadIdx.x == 0) {
     s_found = *D.n_found;
@@ -408,7 +416,7 @@ __global__ void __launch_bounds__(kStreamThreads)
     float cur[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) cur[t] = nx[t];
-    if (i + blockDim.x < I.i1) load_raw(D, i + blockDim.x, nx);
+    if (i + blockDim.x < I.i1) load_raw(Pp, Qp, i + blockDim.x, nx);
     PairGeom g;
     pair_geom(cur, g);
     ndeg += g.deg;
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(kStreamThreads)
       int bin = -1;
       if (!g.deg) {
         bool gate = true;
-        if (D.w >= 0) {
+        if (gw >= 0) {
           float gmin, gmax, hmin, hmax;
           quad_range(g.d3, 2.f * g.d1, W.u0, W.u1, gmin, gmax);
           quad_range(g.d3, 2.f * g.d2, W.v0, W.v1, hmin, hmax);
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(kStreamThreads)
           }
         }
       }
-      D.bins[(int64_t)a * D.n + i] = (int16_t)bin;
+      bins[(int64_t)a * nn + i] = (int16_t)bin;
     }
   }
   atomicAdd(&s_deg, ndeg);
@@ -599,7 +607,8 @@ struct PairQueues {
     }
   }
   // Queue pair i0 + off for rotation a if sel (called by the whole warp with a uniform a).
-  __device__ __forceinline__ void push(int A, bool sel, int off, const InstDev& D, int64_t i0, int lane) {
+  __device__ __forceinline__ void push(int A, bool sel, int off, const float* __restrict__ P,
+                                      const float* __restrict__ Q, int64_t i0, int lane) {
     const unsigned bal = __ballot_sync(kFull, sel);
     if (!bal) return;
     const int pos = len[A] + __popc(bal & ((1u << lane) - 1u));
@@ -608,7 +617,7 @@ struct PairQueues {
     total[A] += __popc(bal);
     if (len[A] >= 32) {
       __syncwarp();
-      add_qpT(acc[A], D.P, D.Q, i0 + q[A * 64 + lane]);
+      add_qpT(acc[A], P, Q, i0 + q[A * 64 + lane]);
       const int rest = len[A] - 32;
       const int moved = lane < rest ? q[A * 64 + 32 + lane] : 0;
       __syncwarp();
@@ -617,11 +626,12 @@ struct PairQueues {
       len[A] = rest;
     }
   }
-  __device__ __forceinline__ void flush(const InstDev& D, int64_t i0, int lane) {
+  __device__ __forceinline__ void flush(const float* __restrict__ P, const float* __restrict__ Q, int64_t i0,
+                                       int lane) {
     __syncwarp();
 #pragma unroll
     for (int a = 0; a < K; ++a)
-      if (lane < len[a]) add_qpT(acc[a], D.P, D.Q, i0 + q[a * 64 + lane]);
+      if (lane < len[a]) add_qpT(acc[a], P, Q, i0 + q[a * 64 + lane]);
     // the pair count travels in slot 9, once per warp (exact in float32: at most an item's pairs)
 #pragma unroll
     for (int a = 0; a < K; ++a) acc[a][9] = FF{lane == 0 ? (float)total[a] : 0.f, 0.f};
@@ -647,7 +657,14 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   PairQueues<K> pq;
   pq.init(queues[wp]);
-  const int J = D.J;
+  const int J = D.J, window = D.window;
+  // the instance's fields the pair loop uses, held in registers (the loop's stores would
+  // otherwise make every iteration reload them)
+  const float* __restrict__ const Pp = D.P;
+  const float* __restrict__ const Qp = D.Q;
+  const int16_t* __restrict__ const bins = D.bins;
+  uint8_t* __restrict__ const vset = D.vote_set;
+  const int64_t nn = D.n;
   // each warp takes 32 consecutive pairs per iteration
   for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
     const int64_t i = base + lane;
@@ -657,19 +674,19 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
       if (a >= kf) break;
       bool in = false;
       if (valid) {
-        const int b = D.bins[(int64_t)a * D.n + i];
+        const int b = bins[(int64_t)a * nn + i];
         if (b >= 0) {
           int dd = b - bhat[a];
           if (dd < 0) dd = -dd;
           dd = min(dd, J - dd);
-          in = dd <= D.window;
+          in = dd <= window;
         }
-        if (D.vote_set) D.vote_set[(int64_t)a * D.n + i] = in;
+        if (vset) vset[(int64_t)a * nn + i] = in;
       }
-      pq.push(a, in, (int)(i - I.i0), D, I.i0, lane);
+      pq.push(a, in, (int)(i - I.i0), Pp, Qp, I.i0, lane);
     }
   }
-  pq.flush(D, I.i0, lane);
+  pq.flush(Pp, Qp, I.i0, lane);
   block_sums(pq.acc, kf, D.msum + ((int64_t)(blockIdx.x - D.item0) * D.k) * 10);
   // the last item of the instance solves the vote-set rotations
   if (D.done && last_block(&D.done[2], (uint32_t)D.n_items))
@@ -690,8 +707,14 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   // each warp takes 32 consecutive pairs per iteration; the next iteration's loads are issued
   // before the current pairs are processed (the first before the wait for R_init)
+  // the instance's fields the pair loop uses, held in registers (the loop's stores would
+  // otherwise make every iteration reload them)
+  const float* __restrict__ const Pp = D.P;
+  const float* __restrict__ const Qp = D.Q;
+  int32_t* __restrict__ const labels = D.labels;
+  uint8_t* __restrict__ const mask = D.mask;
   float nx[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (I.i0 + 32 * wp + lane < I.i1) load_raw(D, I.i0 + 32 * wp + lane, nx);
+  if (I.i0 + 32 * wp + lane < I.i1) load_raw(Pp, Qp, I.i0 + 32 * wp + lane, nx);
   pdl_wait();
   if (threadIdx.x == 0) s_found = *D.n_found;
   __syncthreads();
@@ -707,7 +730,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     float cur[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) cur[t] = nx[t];
-    if (i + blockDim.x < I.i1) load_raw(D, i + blockDim.x, nx);
+    if (i + blockDim.x < I.i1) load_raw(Pp, Qp, i + blockDim.x, nx);
     int lab = -1;
     if (valid) {
       const float p0 = cur[0], p1 = cur[1], p2 = cur[2];
@@ -724,16 +747,16 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
           lab = a;
         }
       }
-      if (D.labels) D.labels[i] = lab;
-      if (D.mask) D.mask[i] = lab >= 0;
+      if (labels) labels[i] = lab;
+      if (mask) mask[i] = lab >= 0;
     }
 #pragma unroll
     for (int a = 0; a < K; ++a) {
       if (a >= kf) break;
-      pq.push(a, lab == a, (int)(i - I.i0), D, I.i0, lane);
+      pq.push(a, lab == a, (int)(i - I.i0), Pp, Qp, I.i0, lane);
     }
   }
-  pq.flush(D, I.i0, lane);
+  pq.flush(Pp, Qp, I.i0, lane);
   block_sums(pq.acc, kf, D.msum + ((int64_t)D.n_items + (blockIdx.x - D.item0)) * D.k * 10);
   // the last item of the instance solves the refined rotations
   if (D.done && last_block(&D.done[3], (uint32_t)D.n_items))
