@@ -28,17 +28,20 @@
 // normal. Every walk steps from the wider chord toward the narrower one (toward the cap's
 // extreme), so the chord computed on the next line is always the narrower one of the strip.
 //
-// Work split. A CTA owns one row band of the accumulator for one slice of circles: a tile of
-// row differences (two rows' 16-bit counters per 32-bit word) and a tile of column differences
-// (two columns' counters per word) in shared memory, incremented with red.shared.add.u32. A
-// warp loads 32 circles; in phase A each lane prepares its circle for the band (its four caps,
-// culled to where the curve crosses the band and the grid) and stores it in a per-warp table.
-// In phase B the units (one strip) of all row caps, then of all column caps, are cut into
-// segments of at most kSeg and dealt out in rounds, kWalkers segments per lane, walked in lock
-// step. After the slice, prefix sums along the rows and down the columns turn the differences
-// into counts, and the two tiles are added into the slice's partial of the accumulator. The
-// words are summed modulo 2^32: every count of a slice is at most its 65535 circles, so each
-// prefix sum yields the exact pair of 16-bit counts.
+// Work split. A work item is one slice of circles in one orientation and band: the row caps
+// voted into a band of rows, or the column caps voted into a band of columns with the same
+// edges. A persistent CTA takes items from a queue; for each it zeroes a shared tile of
+// differences (two rows' 16-bit counters per 32-bit word for a row band, two columns' for a
+// column band; one pad column or row takes the -1 of a run that ends on the grid's last cell),
+// incremented with red.shared.add.u32. A warp loads 32 circles (the next 32 are loaded before
+// these are walked); in phase A each lane prepares its circle for the item (the caps of the
+// item's orientation, culled to where the curve crosses the band and the grid) and stores it in
+// a per-warp table. In phase B the units (one strip each) of those caps are cut into segments
+// of at most kSeg and dealt out in rounds, kWalkers segments per lane, walked in lock step.
+// After the slice, prefix sums along the rows (or down the columns) turn the differences into
+// counts, and the tile is written to the item's partial of the accumulator. The words are summed
+// modulo 2^32: every count of a slice is at most its 65535 circles, so each prefix sum yields the
+// exact pair of 16-bit counts.
 //
 // Decisions. A crossing's cell is the floor of a float32 root computed with hardware square root
 // and reciprocal approximations (a few ulp). The cell differs from the exact test only when the
