@@ -665,16 +665,26 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
   const int16_t* __restrict__ const bins = D.bins;
   uint8_t* __restrict__ const vset = D.vote_set;
   const int64_t nn = D.n;
-  // each warp takes 32 consecutive pairs per iteration
+  // each warp takes 32 consecutive pairs per iteration; the next iteration's bins are loaded
+  // before the current ones are used
+  int nb[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) nb[a] = (a < kf && I.i0 + 32 * wp + lane < I.i1) ? bins[(int64_t)a * nn + I.i0 + 32 * wp + lane] : -1;
   for (int64_t base = I.i0 + 32 * wp; base < I.i1; base += blockDim.x) {
     const int64_t i = base + lane;
     const bool valid = i < I.i1;
+    int cb[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      cb[a] = nb[a];
+      nb[a] = (a < kf && i + blockDim.x < I.i1) ? bins[(int64_t)a * nn + i + blockDim.x] : -1;
+    }
 #pragma unroll
     for (int a = 0; a < K; ++a) {
       if (a >= kf) break;
       bool in = false;
       if (valid) {
-        const int b = bins[(int64_t)a * nn + i];
+        const int b = cb[a];
         if (b >= 0) {
           int dd = b - bhat[a];
           if (dd < 0) dd = -dd;
