@@ -29,7 +29,10 @@
  *     row-major uint32 [row][col].
  *   - Every call is ordered on the CUDA stream it is given (a cudaStream_t passed as void*,
  *     NULL = the legacy default stream). Calls that return results in host structs
- *     synchronise that stream before returning. Calls on one stream must not be issued
+ *     synchronise that stream before returning. (The legacy default stream cannot be
+ *     captured in a CUDA graph, so a solve given it whose launch sequence is captured or
+ *     replayed, a shape seen before, runs on a stream the library owns, after the work
+ *     already ordered on the default stream.) Calls on one stream must not be issued
  *     concurrently from several host threads; calls on different streams may be.
  *   - Return value: SPROT_OK (0) or a negative status; sprot_status_string() describes it.
  *     On error nothing is written to the outputs except where stated.

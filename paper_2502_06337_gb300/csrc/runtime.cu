@@ -69,6 +69,8 @@ struct VoteTimer {
       std::lock_guard<std::mutex> g(g_timing_mu);
       g_vote_ms += ms;
       g_vote_launches += 1;
+    } else {
+      cudaGetLastError();
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -222,7 +224,7 @@ struct GraphEntry {
 struct Workspace {
   std::mutex mu;
   int device = 0;
-  cudaStream_t stream = nullptr;  // the stream the workspace serves (allocations are ordered on it)
+  cudaStream_t stream = nullptr;  // the stream the workspace serves
   char* dev = nullptr;
   size_t dev_cap = 0;
   char* host = nullptr;  // pinned
@@ -244,6 +246,16 @@ struct Workspace {
     if (!(aux && fork && join)) cudaGetLastError();
     return aux && fork && join;
   }
+  // the stream a solve runs on when the caller passed the legacy default stream (which cannot
+  // be captured in a graph), ordered after the caller's work by an event
+  cudaStream_t own = nullptr;
+  cudaEvent_t own_in = nullptr;
+  bool own_stream() {
+    if (!own && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) own = nullptr;
+    if (!own_in && cudaEventCreateWithFlags(&own_in, cudaEventDisableTiming) != cudaSuccess) own_in = nullptr;
+    if (!(own && own_in)) cudaGetLastError();
+    return own && own_in;
+  }
   bool timing_events() {
     if (!tv0 && cudaEventCreate(&tv0) != cudaSuccess) tv0 = nullptr;
     if (!tv1 && cudaEventCreate(&tv1) != cudaSuccess) tv1 = nullptr;
@@ -260,25 +272,30 @@ struct Workspace {
     if (tv1) cudaEventDestroy(tv1);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (own_in) cudaEventDestroy(own_in);
+    if (own) cudaStreamDestroy(own);
     if (aux) cudaStreamDestroy(aux);
     if (dev) cudaFree(dev);
     if (host) cudaFreeHost(host);
   }
   // Device memory grows geometrically and is allocated and freed in stream order
   // (cudaMallocAsync / cudaFreeAsync): a synchronous cudaFree would wait for the whole device,
-  // stalling the other workspaces' streams (e.g. concurrent server batches).
-  int reserve(size_t dbytes, size_t hbytes) {
+  // stalling the other workspaces' streams (e.g. concurrent server batches). `use` is the
+  // caller's stream: the allocation is ordered before the call's work on it (a solve moved to
+  // the workspace's own stream waits on an event recorded after it); every call synchronises
+  // the stream it ran on before it returns, so no earlier work still reads a freed buffer.
+  int reserve(size_t dbytes, size_t hbytes, cudaStream_t use) {
     if (dbytes > dev_cap || hbytes > host_cap) drop_graphs();  // their addresses are about to change
     if (dbytes > dev_cap) {
       size_t want = std::max(dbytes, dev_cap + dev_cap / 2);
-      if (dev && cudaFreeAsync(dev, stream) != cudaSuccess) {
+      if (dev && cudaFreeAsync(dev, use) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(dev);
       }
       dev = nullptr;
       dev_cap = 0;
       auto alloc = [&](size_t b) {
-        if (cudaMallocAsync(reinterpret_cast<void**>(&dev), b, stream) == cudaSuccess) return true;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&dev), b, use) == cudaSuccess) return true;
         cudaGetLastError();
         dev = nullptr;
         if (cudaMalloc(&dev, b) == cudaSuccess) return true;
@@ -627,7 +644,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
   }
   const size_t dev_bytes = off;
   const size_t host_bytes = align_up(header_end) + (res_end - o_res);
-  status = ws->reserve(dev_bytes, host_bytes);
+  status = ws->reserve(dev_bytes, host_bytes, st);
   if (status != SPROT_OK) return status;
   char* D = ws->dev;
   char* H = ws->host;
@@ -703,6 +720,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
   std::optional<VoteTimer> vt;
   auto enqueue = [&](bool direct) -> bool {
     bool ok = true;
+    cudaGetLastError();  // an earlier call's error, not this solve's (sticky errors stay)
     ok &= ck(cudaMemcpyAsync(D, H, header_end, cudaMemcpyHostToDevice, st));
     ok &= ck(cudaMemsetAsync(D + o_zero, 0, zero_end - o_zero, st));
     for (int i = 0; i < m; ++i) {
@@ -717,10 +735,16 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     }
     if (!ok) return false;
     if (split) ok &= ck(cudaEventRecord(ws->fork, st));  // the first part is on the device
+    // The vote's timing events: while the stream is captured they are recorded as external
+    // events, which become event record nodes that time every replay (the flag is refused
+    // outside a capture).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!direct) ok &= ck(cudaStreamIsCapturing(st, &cs));
+    const unsigned tv_flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (direct)
       vt.emplace(st);
     else
-      ok &= ck(cudaEventRecord(ws->tv0, st));
+      ok &= ck(cudaEventRecordWithFlags(ws->tv0, st, tv_flags));
     launch_axis_vote_runs(dvit, n_first, dinst, dcounter, std::min(n_first, nsm), vote_tile, st);
     if (split) {
       // the second part, copied under the first items' vote (after the first part, so that the
@@ -740,7 +764,7 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
     if (direct)
       vt->stop(st);
     else
-      ok &= ck(cudaEventRecord(ws->tv1, st));
+      ok &= ck(cudaEventRecordWithFlags(ws->tv1, st, tv_flags));
     // each kernel's last block per instance finishes that instance's stage (peaks; angle peak
     // and Rodrigues; the two Kabsch solves)
     launch_grid_reduce(drit, (int)ritems.size(), dinst, st);
@@ -780,6 +804,17 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
                          (uint64_t)plan[i].o_mask, (uint64_t)plan[i].o_labels})
         k2.push_back(v);
     }
+    // The legacy default stream cannot be captured: a solve whose graph is captured or
+    // replayed now runs on the workspace's own stream instead, after everything the caller
+    // ordered before it, the workspace's allocation included (the solve waits for its results
+    // before returning, so the caller's later work follows it). Shapes seen for the first time
+    // run directly on the caller's stream.
+    auto ge = ws->graphs.find(k2);
+    if ((st == nullptr || st == cudaStreamLegacy) && ge != ws->graphs.end() &&
+        (ge->second.exec || ge->second.capturable) && ws->own_stream()) {
+      if (!ck(cudaEventRecord(ws->own_in, st)) || !ck(cudaStreamWaitEvent(ws->own, ws->own_in, 0))) return SPROT_E_CUDA;
+      st = ws->own;
+    }
     ok = run_graph(ws.get(), k2, st, [&] { return enqueue(false); });
   }
   if (!ok || !ck(cudaStreamSynchronize(st))) return SPROT_E_CUDA;
@@ -791,6 +826,8 @@ int solve(std::vector<Problem>& probs, cudaStream_t st, bool graphs, const sprot
       std::lock_guard<std::mutex> g(g_timing_mu);
       g_vote_ms += ms;
       g_vote_launches += 1;
+    } else {
+      cudaGetLastError();
     }
   }
   int worst = SPROT_OK;
@@ -857,7 +894,7 @@ int axis_vote_only(const float* P, const float* Q, int64_t n, int G, uint32_t* g
   size_t o_zero = take(sizeof(int)), o_peak = take(8);
   size_t zend = off;
   size_t o_part = take((size_t)kinds * ip.S * G * (G / 2) * 4);
-  status = ws->reserve(off, hdr);
+  status = ws->reserve(off, hdr, st);
   if (status != SPROT_OK) return status;
   char* D = ws->dev;
   char* H = ws->host;
@@ -912,7 +949,7 @@ int select_peaks(const uint32_t* grid, int G, int k, float nms_deg, int32_t* cel
   size_t o_inst = take(sizeof(InstDev)), o_rit = take(sizeof(ReduceItem) * rit.size());
   size_t hdr = off;
   size_t o_peak = take(8 * (size_t)k);
-  status = ws->reserve(off, hdr);
+  status = ws->reserve(off, hdr, st);
   if (status != SPROT_OK) return status;
   char* D = ws->dev;
   char* H = ws->host;
@@ -1052,7 +1089,7 @@ int sprot_refine_axis(const float* P, const float* Q, int64_t n, const int32_t* 
   const int chunk = kStreamChunk;
   const int nb = (int)((n + chunk - 1) / chunk);
   const size_t part_bytes = align_up(sizeof(double) * 8 * (size_t)nb);
-  status = ws->reserve(part_bytes + align_up(sizeof(double) * 8), align_up(sizeof(double) * 8));
+  status = ws->reserve(part_bytes + align_up(sizeof(double) * 8), align_up(sizeof(double) * 8), st);
   if (status != SPROT_OK) return status;
   double* dpart = reinterpret_cast<double*>(ws->dev);
   double* dout = reinterpret_cast<double*>(ws->dev + part_bytes);

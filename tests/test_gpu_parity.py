@@ -255,6 +255,39 @@ def test_pinned_host_buffers_reused_with_new_contents_and_sizes(lib):
             assert got["n_inliers"] == want["n_inliers"] and np.array_equal(got["R"], want["R"])
 
 
+def test_default_stream_graph_replay_with_timing_then_host_mask(lib):
+    """Solves on the legacy default stream replay a CUDA graph on the library's own stream
+    (the legacy stream cannot be captured): with vote timing on, every replay is timed, and
+    a following solve from pinned host buffers that also returns the inlier mask gives the
+    device solve's rotation, inliers and mask."""
+    from paper_2502_06337_gb300 import binding as B
+    import torch
+
+    n = 300_000
+    prob = synth.make_problem(n, (0.1,), 0.01, seed=64)
+    P, Q = torch.from_numpy(prob.P).cuda(), torch.from_numpy(prob.Q).cuda()
+    prm = B.make_params(grid=512, angle_bins=720, tau=0.052)
+    m_d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    want = B.estimate_rotation(P, Q, prm, mask=m_d)
+    B.kernel_timing(True)
+    try:
+        for _ in range(4):  # direct, captured, then replayed
+            got = B.estimate_rotation(P, Q, prm, mask=m_d)
+            assert got["cell"] == want["cell"] and np.array_equal(got["R"], want["R"])
+        ms, launches = B.kernel_timing_read()
+    finally:
+        B.kernel_timing(False)
+    assert launches == 4 and ms > 0.0
+    Ph, Qh = torch.from_numpy(prob.P).pin_memory(), torch.from_numpy(prob.Q).pin_memory()
+    m_h = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    prm_h = B.make_params(grid=512, angle_bins=720, tau=0.052, flags=B.HOST_PTRS)
+    for _ in range(3):
+        got = B.estimate_rotation(Ph.numpy(), Qh.numpy(), prm_h, mask=m_h.numpy())
+        assert got["cell"] == want["cell"] and got["n_inliers"] == want["n_inliers"]
+        assert np.array_equal(got["R"], want["R"])
+        assert np.array_equal(m_h.numpy(), m_d.cpu().numpy())
+
+
 def test_pinned_host_pointers_multi_rotation(lib):
     from paper_2502_06337_gb300 import binding as B
     import torch
