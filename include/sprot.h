@@ -209,6 +209,13 @@ int sprot_axis_vote_noalloc(const float* P, const float* Q, int64_t n, int32_t g
 int sprot_vote_plan(int64_t n, int32_t grid_size, int32_t batched, int32_t* n_bands,
                     int32_t* band_row0, int32_t* slices);
 
+/* sprot_vote_plan for a device with n_sm streaming multiprocessors (1 <= n_sm <= 4096), given
+ * instead of read from the current device: the same split that device would get. Pure host
+ * code; makes no CUDA call, so it runs without a GPU. Errors: E_INVAL (as sprot_vote_plan, or
+ * n_sm out of range). */
+int sprot_vote_plan_sm(int64_t n, int32_t grid_size, int32_t batched, int32_t n_sm,
+                       int32_t* n_bands, int32_t* band_row0, int32_t* slices);
+
 /* The consensus accumulator of Eq. 9 at cell resolution: grid[G*G] (device uint32) = the
  * number of non-degenerate pairs for which some axis r of the closed cell has
  * |r . z_i| < eps, z_i = (p_i - q_i)/|p_i - q_i| (the cells within angular distance asin(eps)

@@ -28,7 +28,8 @@ EXPORTS = [
     "sprot_select_peaks", "sprot_estimate_batch", "sprot_autotune_grid", "sprot_server_create",
     "sprot_server_submit", "sprot_server_wait", "sprot_server_destroy",
     "sprot_release_workspaces", "sprot_release_stream_workspace", "sprot_kernel_launch_count", "sprot_probe_smem_atomic_rate",
-    "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan", "sprot_axis_vote_noalloc",
+    "sprot_kernel_timing", "sprot_kernel_timing_read", "sprot_vote_plan", "sprot_vote_plan_sm",
+    "sprot_axis_vote_noalloc",
     "sprot_default_knobs", "sprot_autotune_plan", "sprot_autotune_batch", "sprot_tuned_plan",
     "sprot_set_tuned_plan", "sprot_autotune_reset", "sprot_server_request_bytes",
 ]
@@ -122,6 +123,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_axis_vote_sampled.argtypes = [vp, vp, i64, i32, i32, vp, vp]
     lib.sprot_axis_vote_eps.argtypes = [vp, vp, i64, i32, C.c_float, vp, vp]
     lib.sprot_vote_plan.argtypes = [i64, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.sprot_vote_plan_sm.argtypes = [i64, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.sprot_axis_vote_noalloc.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.sprot_refine_axis.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i64), vp]
@@ -156,7 +158,7 @@ def load(path: str = LIB_PATH):
     lib.sprot_kernel_timing_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
     lib.sprot_kernel_timing_read.restype = None
     for name in ["sprot_estimate_rotation", "sprot_estimate_rotations_k", "sprot_estimate_rotations_ex",
-                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_axis_vote_noalloc", "sprot_axis_vote_eps", "sprot_refine_axis",
+                 "sprot_axis_vote", "sprot_axis_vote_sampled", "sprot_vote_plan", "sprot_vote_plan_sm", "sprot_axis_vote_noalloc", "sprot_axis_vote_eps", "sprot_refine_axis",
                  "sprot_select_peaks",
                  "sprot_estimate_batch", "sprot_autotune_plan", "sprot_autotune_batch", "sprot_set_tuned_plan",
                  "sprot_server_create", "sprot_server_submit", "sprot_server_wait",
@@ -249,12 +251,17 @@ def axis_vote(P, Q, G: int, grid, stream=None):
     check(st, "sprot_axis_vote")
 
 
-def vote_plan(n: int, G: int, batched: bool = False):
-    """The axis vote's work split for n pairs on a G x G grid: dict(band_row0, slices)."""
+def vote_plan(n: int, G: int, batched: bool = False, n_sm: int | None = None):
+    """The axis vote's work split for n pairs on a G x G grid: dict(band_row0, slices), for the
+    current device, or without a GPU for a device of ``n_sm`` SMs."""
     nb, sl = C.c_int32(0), C.c_int32(0)
     rows = (C.c_int32 * (MAX_BANDS + 1))()
-    check(load().sprot_vote_plan(int(n), int(G), 1 if batched else 0, C.byref(nb), rows, C.byref(sl)),
-          "sprot_vote_plan")
+    if n_sm is None:
+        check(load().sprot_vote_plan(int(n), int(G), 1 if batched else 0, C.byref(nb), rows, C.byref(sl)),
+              "sprot_vote_plan")
+    else:
+        check(load().sprot_vote_plan_sm(int(n), int(G), 1 if batched else 0, int(n_sm), C.byref(nb), rows,
+                                        C.byref(sl)), "sprot_vote_plan_sm")
     return dict(band_row0=list(rows[:nb.value + 1]), slices=sl.value)
 
 

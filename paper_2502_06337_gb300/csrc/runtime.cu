@@ -1050,24 +1050,36 @@ int sprot_axis_vote(const float* P, const float* Q, int64_t n, int32_t G, uint32
   return axis_vote_only(P, Q, n, G, grid, reinterpret_cast<cudaStream_t>(stream), -1.f);
 }
 
-int sprot_vote_plan(int64_t n, int32_t G, int32_t batched, int32_t* n_bands, int32_t* band_row0,
-                    int32_t* slices) {
-  if (!n_bands || !band_row0 || !slices || n < 1 || n > (int64_t)1 << 31 || !is_pow2(G) ||
-      G < SPROT_MIN_GRID || G > SPROT_MAX_GRID)
-    return SPROT_E_INVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return SPROT_E_CUDA;
-  }
+namespace {
+bool vote_plan_args_ok(int64_t n, int32_t G, const int32_t* n_bands, const int32_t* band_row0,
+                       const int32_t* slices) {
+  return n_bands && band_row0 && slices && n >= 1 && n <= (int64_t)1 << 31 && is_pow2(G) &&
+         G >= SPROT_MIN_GRID && G <= SPROT_MAX_GRID;
+}
+}  // namespace
+
+int sprot_vote_plan_sm(int64_t n, int32_t G, int32_t batched, int32_t n_sm, int32_t* n_bands,
+                       int32_t* band_row0, int32_t* slices) {
+  if (!vote_plan_args_ok(n, G, n_bands, band_row0, slices) || n_sm < 1 || n_sm > 4096) return SPROT_E_INVAL;
   InstPlan ip{};
   ip.G = G;
-  plan_vote(ip, n, batched == 0, sm_count(dev));
+  plan_vote(ip, n, batched == 0, n_sm);
   if (ip.T <= 0) return SPROT_E_INVAL;
   *n_bands = ip.T;
   for (int b = 0; b <= ip.T; ++b) band_row0[b] = ip.row0[b];
   *slices = ip.S;
   return SPROT_OK;
+}
+
+int sprot_vote_plan(int64_t n, int32_t G, int32_t batched, int32_t* n_bands, int32_t* band_row0,
+                    int32_t* slices) {
+  if (!vote_plan_args_ok(n, G, n_bands, band_row0, slices)) return SPROT_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SPROT_E_CUDA;
+  }
+  return sprot_vote_plan_sm(n, G, batched, sm_count(dev), n_bands, band_row0, slices);
 }
 
 int sprot_axis_vote_eps(const float* P, const float* Q, int64_t n, int32_t G, float eps, uint32_t* grid,
