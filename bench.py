@@ -35,6 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Mcorr/s axis+angle vote (n=1e6, 90% outl.); served solves/s, p50/p99 ms"
+WORKLOAD = "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins"
 UNIT = "Mcorr/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
 
@@ -299,7 +300,7 @@ def run_sprot(args):
         "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "dtype_detail": "f32 geometry, u32 vote counts, f64 least-squares refinement",
         "data": "synthetic (seeded; uniform cube points, uniform random rotation)",
-        "config": {"workload": "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins",
+        "config": {"workload": WORKLOAD,
                    "n": n, "grid": G, "angle_bins": J, "tau": tau, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (512 MB write outside the timed events)"},
         "result": {"cell": rot["cell"], "bin": rot["bin"], "axis_votes": rot["axis_votes"],
@@ -439,7 +440,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "single rotation, n=1e6, 90% outliers, sigma=0.01, 512x512 grid, 720 angle bins",
+        "data": "synthetic", "config": {"workload": WORKLOAD,
                                         "n": prob.n, "grid": G, "angle_bins": J},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                          "sample": f"each step: FP64 oracle on the first {n_s} correspondences, "

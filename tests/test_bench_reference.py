@@ -1,0 +1,32 @@
+"""The bench's reference arm without a GPU (not gpu): `bench.py --impl reference` times the FP64
+oracle on the host's cores and prints one JSON line on the same metric, unit and workload as
+the library's arm, with its CPU sample described, and an e2e entry that moves no bytes."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout[-2000:]
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference"
+    assert r["metric"] == bench.METRIC and r["unit"] == bench.UNIT == "Mcorr/s"
+    assert r["config"]["workload"] == bench.WORKLOAD
+    assert (r["config"]["n"], r["config"]["grid"], r["config"]["angle_bins"]) == (1_000_000, 512, 720)
+    assert r["higher_is_better"] is True and r["n_gpus"] == 1
+    assert (r["steps"], r["warmup"]) == (1, 3)
+    assert r["value"] > 0 and r["ms_per_step"] > 0
+    assert r["dtype"] == "f64" and r["vs_baseline"] is None
+    cb = r["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    assert r["e2e"] == {"value": r["value"], "unit": "Mcorr/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
