@@ -33,8 +33,8 @@ def test_reference_arm_json_line():
 
 
 def test_reference_arm_under_two_ranks_prints_once():
-    """Launched as the driver launches N > 1 (one process per rank): rank 0 alone runs the
-    oracle and prints the line, with n_gpus = 2; the other rank exits 0 without work."""
+    """Launched for N = 2 with torchrun (one process per rank): rank 0 alone runs the oracle and
+    prints the line, with n_gpus = 2; the other rank exits 0 without work."""
     import socket
 
     with socket.socket() as sk:  # a free port for the rendezvous
