@@ -49,3 +49,30 @@ def test_reference_arm_under_two_ranks_prints_once():
     assert len(lines) == 1, out.stdout[-2000:]
     r = json.loads(lines[0])
     assert r["impl"] == "reference" and r["n_gpus"] == 2 and r["value"] > 0
+
+
+def test_vote_traffic_record_is_dropped_once_the_kernel_changes(tmp_path, monkeypatch):
+    """The roofline's `traffic` comes from the committed ncu record of the axis-vote kernel only
+    while the kernel's source is the one the counters were taken on (its sha256); a changed
+    source gives no record, so the line reports traffic null."""
+    import hashlib
+    import shutil
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    rec = json.load(open(os.path.join(ROOT, "profiles", "axis_vote_traffic.json")))
+    assert rec["workload"] == bench.WORKLOAD
+    for key in ("dram_bytes_per_launch", "warp_instructions_per_launch", "grid_ctas", "command"):
+        assert key in rec
+    # a copy of the tree with the record and the kernel source
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_2502_06337_gb300" / "csrc").mkdir(parents=True)
+    shutil.copy(os.path.join(ROOT, "profiles", "axis_vote_traffic.json"), tmp_path / "profiles")
+    src = tmp_path / "paper_2502_06337_gb300" / "csrc" / "vote_runs.cu"
+    shutil.copy(os.path.join(ROOT, "paper_2502_06337_gb300", "csrc", "vote_runs.cu"), src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    same = hashlib.sha256(src.read_bytes()).hexdigest() == rec["kernel_source_sha256"]
+    assert bench.vote_profile() == (rec if same else {})
+    src.write_bytes(src.read_bytes() + b"\n// changed\n")
+    assert bench.vote_profile() == {}
